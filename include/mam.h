@@ -1,0 +1,219 @@
+/*
+ * mam.h - C ABI of libmam, a GB300 (sm_103a) implementation of the Method of
+ * Averaged Marginals (MAM) for fixed-support balanced and unbalanced
+ * Wasserstein barycenters (Mimouni, Malisani, Zhu, de Oliveira,
+ * arXiv 2309.05315).
+ *
+ * Problem (eq. HugeLP, eq. UWB):  M discrete measures
+ *   nu^(m) = sum_s q^(m)_s delta_{zeta^(m)_s},  s = 1..S_m,
+ * a fixed barycenter support xi_1..xi_R, weights alpha_m and costs
+ *   c^(m)_{rs} = alpha_m * ||xi_r - zeta^(m)_s||^2   (or alpha_m * C^(m)_{rs}).
+ * The library runs Algorithm 1 (MAM): Step 1 averages the row marginals of
+ * the plans theta^(m) with the weights a_m of eq. (pr) (Prop. 2), the factor
+ * t^k of Algorithm 1 switches between the balanced (gamma = inf) and the
+ * unbalanced prox of eq. (Unbalanced-prox), Step 2 projects every plan
+ * column onto the scaled simplex Delta_R(q_s) (Prop. 3, Remark 1) and
+ * updates theta, Step 3 recomputes the marginals.  Index sets follow
+ * Remark 2 (random bundles) or are all measures (deterministic MAM).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns mam_status; no C++ exception crosses the ABI.
+ *   On failure a message is available from mam_last_error(handle) (or
+ *   mam_last_error(NULL) for a failed create, thread-local).
+ * - Ownership: inputs are copied during the call; caller buffers may be
+ *   freed as soon as the call returns.  The library owns every device buffer
+ *   it allocates (plans, costs, marginals, scratch) and frees them in
+ *   mam_destroy.  Outputs go to caller-provided buffers.
+ * - Streams: all device work of a handle is ordered on its stream
+ *   (mam_desc.stream, or a stream the library creates when NULL).  Only
+ *   mam_objective, mam_solve, the mam_get_* calls and mam_backward
+ *   synchronise that stream.
+ * - Layout: supports are given measure after measure, unpruned (zero
+ *   weights allowed): measure m occupies entries off_m .. off_m + S_m - 1
+ *   where off_m = S_0 + ... + S_{m-1}.  Point arrays are row-major
+ *   [n][dim].  Plans are stored pruned and column-contiguous: column s of
+ *   measure m is R consecutive floats.
+ * - Errors: invalid arguments -> MAM_ERR_INVALID_ARG with nothing
+ *   allocated; device allocation failure -> MAM_ERR_OOM with nothing
+ *   leaked; a CUDA error -> MAM_ERR_CUDA and the handle enters the error
+ *   state, in which every later call except mam_destroy/mam_last_error
+ *   returns MAM_ERR_STATE.  A non-finite residual -> MAM_ERR_NONFINITE.  A
+ *   device-side wait that exceeded its bound -> MAM_ERR_TIMEOUT.
+ */
+#ifndef MAM_H_
+#define MAM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MAM_OK = 0,
+  MAM_ERR_INVALID_ARG = 1,
+  MAM_ERR_CUDA = 2,
+  MAM_ERR_OOM = 3,
+  MAM_ERR_NONFINITE = 4,
+  MAM_ERR_TIMEOUT = 5,
+  MAM_ERR_STATE = 6,
+  MAM_ERR_UNSUPPORTED = 7
+} mam_status;
+
+/* Storage type of the cost c (theta is always FP32; p, objective and
+ * residuals are FP64).  Costs are computed in FP64, rounded to FP32 (nearest)
+ * and then, for BF16/F16, rounded again to nearest-even. */
+typedef enum { MAM_F32 = 0, MAM_BF16 = 1, MAM_F16 = 2 } mam_cost_dtype;
+
+/* When the fused diagnostics (W-hat, dist_L(pi-hat), lower bound, residuals)
+ * are computed. */
+typedef enum {
+  MAM_DIAG_LAST = 0,   /* last iteration of every mam_step call (default) */
+  MAM_DIAG_NEVER = 1,  /* never (fastest; mam_objective then reports iter=-1) */
+  MAM_DIAG_EVERY = 2   /* every iteration */
+} mam_diag_mode;
+
+typedef struct mam_problem mam_problem; /* opaque, library-owned */
+
+/* Problem description (eq. HugeLP / eq. UWB data plus MAM parameters). */
+typedef struct {
+  int32_t M;            /* number of measures, >= 1                          */
+  int32_t R;            /* barycenter support size, >= 1                     */
+  int32_t dim;          /* point dimension, 1..3                             */
+  const int32_t* S;     /* host [M]: support sizes BEFORE pruning, >= 1      */
+  const double* zeta;   /* host [sum S][dim]: support points of the measures */
+  const double* q;      /* host [sum S]: weights q^(m)_s >= 0, finite; columns
+                           with q = 0 are pruned (Section 4.3); every measure
+                           needs at least one positive weight               */
+  const double* alpha;  /* host [M]: alpha_m >= 0, folded into the cost      */
+  const double* xi;     /* host [R][dim]: barycenter support points          */
+  const double* cost;   /* host [sum S][R] general cost C (row s of measure m
+                           = column s of C^(m)), or NULL for squared
+                           Euclidean.  Scaled by alpha_m either way.         */
+  double rho;           /* prox parameter of eq. (DR), > 0: the projected
+                           vector is theta + 2 t d - c / rho (Alg. 1)        */
+  double gamma;         /* unbalanced penalty >= 0; INFINITY = balanced.
+                           Balanced problems need equal total masses.        */
+  int32_t n_bundles;    /* 0 or 1: deterministic MAM (all measures each
+                           iteration).  nb > 1: Remark 2, measures split into
+                           nb contiguous bundles, bundle i drawn with
+                           probability sum_{m in A_i} alpha_m.               */
+  uint64_t seed;        /* seed of the bundle draws (counter-based
+                           SplitMix64; draw k uses seed + k*0x9E3779B97F4A7C15) */
+  int32_t cost_dtype;   /* mam_cost_dtype                                    */
+  int32_t theta0_mode;  /* 0: theta^0_{rs} = q_s / R;  1: theta^0 = 0       */
+  int32_t diag_mode;    /* mam_diag_mode                                     */
+  void* stream;         /* cudaStream_t to order work on, or NULL            */
+} mam_desc;
+
+/* Diagnostics of the most recent diagnostic iteration k (all FP64). */
+typedef struct {
+  double w_hat;        /* sum_m <c^(m), pi-hat^(m)>                         */
+  double dist_pihat;   /* dist_L(pi-hat) = sqrt(sum_m ||p^ - p^^(m)||^2/S_m) */
+  double lower_bound;  /* sum_m sum_s q_s min_r (c_rs - rho d^(m)_r): a valid
+                          lower bound of eq. (HugeLP)/(UWB) (deterministic
+                          runs; randomized runs recompute it on demand)     */
+  double f_unbal;      /* w_hat + gamma * dist_pihat (= w_hat if balanced) */
+  double fp_resid;     /* ||theta^{k+1} - theta^k||_2 over updated columns  */
+  double dp_norm;      /* ||p^{k+1} - p^k||_2                               */
+  double t;            /* t^k of Algorithm 1 used by iteration k            */
+  double dist_theta;   /* dist_L(theta^k) (text after Algorithm 1)          */
+  int64_t iter;        /* k + 1 = iterations done when measured, -1: none   */
+  int64_t newton_passes; /* threshold-search passes summed over columns     */
+} mam_objective_t;
+
+/* Create a problem: validates, prunes zero-weight columns, builds the cost
+ * on the device, sets theta^0 and the Step 0 marginals.  On failure *out is
+ * NULL and nothing is leaked.  Cites: eq. (HugeLP), Section 4.3, Alg. 1
+ * Step 0. */
+mam_status mam_create(const mam_desc* desc, mam_problem** out);
+
+/* Batch of n independent problems solved together: every iteration is one
+ * launch of the column kernel over all problems' columns plus one averaging
+ * launch, replayed from a captured CUDA graph.  All problems must share R,
+ * dim, cost_dtype and diag_mode and be deterministic (n_bundles <= 1).  The
+ * stream of descs[0] is used. */
+mam_status mam_batch_create(int32_t n, const mam_desc* descs, mam_problem** out);
+
+/* Run n_iters iterations of Algorithm 1 (asynchronous on the stream). */
+mam_status mam_step(mam_problem* h, int32_t n_iters);
+
+/* Iterate until gap <= gap_tol (checked every check_every iterations, which
+ * must be >= 1) or max_iters.  gap = max(|F - ref| / |ref|,
+ * dist_L(pi-hat) / Q) where F = f_unbal, Q = total mass and ref = w_ref if
+ * w_ref > 0, else the lower bound (a certified gap when F is an upper
+ * bound).  *iters_done (may be NULL) receives the iterations run; *gap_out
+ * (may be NULL) the last gap.  Batched handles use the largest gap. */
+mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol,
+                     double w_ref, int32_t check_every, int32_t* iters_done,
+                     double* gap_out);
+
+/* Diagnostics of problem `index` (0 for a single problem); synchronises. */
+mam_status mam_objective(mam_problem* h, int32_t index, mam_objective_t* out);
+
+/* Barycenter p = sum_m a_m p^(m) of the current theta (Alg. 1 "Return"),
+ * [n_problems][R] FP64.  device_ptr != 0: p_out is a device pointer. */
+mam_status mam_get_barycenter(mam_problem* h, double* p_out, int32_t device_ptr);
+
+/* Current plans, pruned and column-contiguous: [T][R] FP32 where T is the
+ * number of kept columns (mam_get_sizes).  Host pointer. */
+mam_status mam_get_theta(mam_problem* h, float* theta_out);
+
+/* Sizes: n_problems, total measures, R, kept columns T, padded column
+ * stride (floats) of the device plan buffer.  Any pointer may be NULL. */
+mam_status mam_get_sizes(const mam_problem* h, int32_t* n_problems,
+                         int32_t* n_measures, int32_t* R, int64_t* T,
+                         int32_t* ld);
+
+/* Kept (pruned) column count of every measure, [total measures]. */
+mam_status mam_get_pruned_sizes(const mam_problem* h, int32_t* S_out);
+
+/* Checkpoint: the whole iteration state (theta, marginals, thresholds,
+ * iteration counter, bundle position).  Call with buf = NULL to get *bytes.
+ * Resuming with mam_set_state reproduces an uninterrupted run bit for bit. */
+mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes);
+mam_status mam_set_state(mam_problem* h, const void* buf, size_t bytes);
+
+/* Differentiation through K unrolled iterations (balanced, deterministic,
+ * single problem).  mam_forward_record restarts from theta^0, runs K
+ * iterations and keeps theta every ckpt_every iterations.  mam_backward
+ * takes dL/dp^K [R] and writes dL/dq [sum S] (unpruned order, zeros for
+ * pruned columns), dL/dzeta [sum S][dim] and dL/dxi [R][dim]; any output may
+ * be NULL.  All host pointers.  Only squared Euclidean costs with
+ * theta0_mode 0 or 1. */
+mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every);
+mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
+                        double* grad_zeta, double* grad_xi);
+
+/* Kernel configuration: threads per column (multiple of 32, <= 1024),
+ * float4 vectors per thread (1..8), pipeline stages (2..4), CTAs per SM
+ * (0 = occupancy maximum), and the bisection depth used on a cold start
+ * (0..30).  Returns MAM_ERR_INVALID_ARG for a configuration that cannot
+ * cover R. */
+typedef struct {
+  int32_t threads;
+  int32_t vec;
+  int32_t stages;
+  int32_t ctas_per_sm;
+  int32_t bisect_depth;
+} mam_kernel_config;
+mam_status mam_get_config(const mam_problem* h, mam_kernel_config* cfg);
+mam_status mam_set_config(mam_problem* h, const mam_kernel_config* cfg);
+
+/* Time every candidate configuration for `iters` iterations on a copy of the
+ * state (the state is restored afterwards) and keep the fastest. */
+mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best);
+
+/* Last error message of h, or the thread-local one when h is NULL. */
+const char* mam_last_error(const mam_problem* h);
+
+/* Free everything the handle owns; NULL is allowed. */
+void mam_destroy(mam_problem* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAM_H_ */
