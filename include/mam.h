@@ -80,7 +80,7 @@ typedef struct mam_problem mam_problem; /* opaque, library-owned */
 /* Problem description (eq. HugeLP / eq. UWB data plus MAM parameters). */
 typedef struct {
   int32_t M;            /* number of measures, >= 1                          */
-  int32_t R;            /* barycenter support size, >= 1                     */
+  int32_t R;            /* barycenter support size, 1..12288                 */
   int32_t dim;          /* point dimension, 1..3                             */
   const int32_t* S;     /* host [M]: support sizes BEFORE pruning, >= 1      */
   const double* zeta;   /* host [sum S][dim]: support points of the measures */
@@ -119,7 +119,9 @@ typedef struct {
   double fp_resid;     /* ||theta^{k+1} - theta^k||_2 over updated columns  */
   double dp_norm;      /* ||p^{k+1} - p^k||_2                               */
   double t;            /* t^k of Algorithm 1 used by iteration k            */
-  double dist_theta;   /* dist_L(theta^k) (text after Algorithm 1)          */
+  double dist_theta;   /* dist_L(theta) of the current plans (text after
+                          Algorithm 1)                                      */
+  double t_next;       /* t of the next iteration (from the current plans)  */
   int64_t iter;        /* k + 1 = iterations done when measured, -1: none   */
   int64_t newton_passes; /* threshold-search passes summed over columns     */
 } mam_objective_t;
@@ -156,6 +158,10 @@ mam_status mam_objective(mam_problem* h, int32_t index, mam_objective_t* out);
 /* Barycenter p = sum_m a_m p^(m) of the current theta (Alg. 1 "Return"),
  * [n_problems][R] FP64.  device_ptr != 0: p_out is a device pointer. */
 mam_status mam_get_barycenter(mam_problem* h, double* p_out, int32_t device_ptr);
+
+/* Row marginals p^(m) = sum_s theta^(m)_{.s} of the current plans (Alg. 1
+ * Step 3), [total measures][R] FP64.  device_ptr != 0: device pointer. */
+mam_status mam_get_marginals(mam_problem* h, double* pm_out, int32_t device_ptr);
 
 /* Current plans, pruned and column-contiguous: [T][R] FP32 where T is the
  * number of kept columns (mam_get_sizes).  Host pointer. */
@@ -205,6 +211,15 @@ mam_status mam_set_config(mam_problem* h, const mam_kernel_config* cfg);
 /* Time every candidate configuration for `iters` iterations on a copy of the
  * state (the state is restored afterwards) and keep the fastest. */
 mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best);
+
+/* Measurement support: while enabled, every iteration is launched on its own
+ * (no graph replay) between CUDA events on the handle's stream, so that the
+ * durations of the column kernel and of the averaging kernel can be read
+ * back.  mam_profile_read synchronises, returns the summed milliseconds and
+ * the number of iterations timed since the last read, and resets them. */
+mam_status mam_profile_enable(mam_problem* h, int32_t enable);
+mam_status mam_profile_read(mam_problem* h, double* column_ms, double* average_ms,
+                            int64_t* launches);
 
 /* Last error message of h, or the thread-local one when h is NULL. */
 const char* mam_last_error(const mam_problem* h);

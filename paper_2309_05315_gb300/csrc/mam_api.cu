@@ -1,0 +1,1119 @@
+// libmam host side: the C ABI of include/mam.h.
+//
+// Responsibilities: argument validation, pruning of zero-weight columns
+// (Section 4.3 "Storage complexity"), the device layout (plans and costs
+// column-contiguous with a padded stride), the persistent-grid work
+// schedules, the iteration driver (Algorithm 1 replayed from a captured CUDA
+// graph), diagnostics, checkpoints and kernel configuration.
+#include "mam.h"
+#include "mam_internal.h"
+#include "mam_handle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace mam;
+
+namespace mam {
+
+thread_local std::string g_last_error;
+
+mam_status fail(mam_problem* h, mam_status code, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (code == MAM_ERR_CUDA || code == MAM_ERR_TIMEOUT) h->failed = true;
+  } else {
+    g_last_error = msg;
+  }
+  return code;
+}
+
+mam_status cuda_fail(mam_problem* h, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return fail(h, MAM_ERR_OOM, msg);
+  }
+  return fail(h, MAM_ERR_CUDA, msg);
+}
+
+template <typename T>
+mam_status upload(mam_problem* h, T* dst, const T* src, size_t count) {
+  if (count == 0) return MAM_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(T),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "upload");
+  return MAM_OK;
+}
+
+size_t cost_elem_size(int dt) { return dt == MAM_F32 ? 4 : 2; }
+
+}  // namespace mam
+
+#define MAM_TRY(x)                     \
+  do {                                 \
+    mam_status _s = (x);               \
+    if (_s != MAM_OK) return _s;       \
+  } while (0)
+
+#define MAM_CUDA(x, where)                                \
+  do {                                                    \
+    cudaError_t _e = (x);                                 \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
+  } while (0)
+
+namespace {
+
+bool finite_all(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+mam_status validate(const mam_desc* d, int idx) {
+  const std::string p = "desc[" + std::to_string(idx) + "]: ";
+  if (!d) return fail(nullptr, MAM_ERR_INVALID_ARG, p + "null descriptor");
+  if (d->M < 1) return fail(nullptr, MAM_ERR_INVALID_ARG, p + "M must be >= 1");
+  if (d->R < 1) return fail(nullptr, MAM_ERR_INVALID_ARG, p + "R must be >= 1");
+  if (d->R > kMaxR)
+    return fail(nullptr, MAM_ERR_INVALID_ARG,
+                p + "R must be <= " + std::to_string(kMaxR) +
+                    " (one CTA holds a whole column in registers)");
+  if (d->dim < 1 || d->dim > 3)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "dim must be 1..3");
+  if (!d->S || !d->q || !d->alpha || !d->xi)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "S, q, alpha and xi are required");
+  if (!d->zeta && !d->cost)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "zeta is required without a cost matrix");
+  if (!(d->rho > 0) || !std::isfinite(d->rho))
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "rho must be finite and > 0");
+  if (std::isnan(d->gamma) || d->gamma < 0)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "gamma must be >= 0 (or INFINITY)");
+  if (d->cost_dtype < 0 || d->cost_dtype > 2)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "unknown cost_dtype");
+  if (d->theta0_mode < 0 || d->theta0_mode > 1)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "theta0_mode must be 0 or 1");
+  if (d->diag_mode < 0 || d->diag_mode > 2)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "unknown diag_mode");
+  if (d->n_bundles < 0 || d->n_bundles > d->M)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "n_bundles must be in 0..M");
+  long long tot = 0;
+  for (int m = 0; m < d->M; ++m) {
+    if (d->S[m] < 1)
+      return fail(nullptr, MAM_ERR_INVALID_ARG, p + "every S_m must be >= 1");
+    tot += d->S[m];
+  }
+  if (!finite_all(d->q, size_t(tot)) || !finite_all(d->alpha, size_t(d->M)) ||
+      !finite_all(d->xi, size_t(d->R) * d->dim) ||
+      (d->zeta && !finite_all(d->zeta, size_t(tot) * d->dim)))
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "non-finite input");
+  if (d->cost && !finite_all(d->cost, size_t(tot) * d->R))
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "non-finite cost");
+  for (int m = 0; m < d->M; ++m)
+    if (d->alpha[m] < 0)
+      return fail(nullptr, MAM_ERR_INVALID_ARG, p + "alpha must be >= 0");
+  long long off = 0;
+  double Q0 = 0;
+  for (int m = 0; m < d->M; ++m) {
+    double Q = 0;
+    int pos = 0;
+    for (int s = 0; s < d->S[m]; ++s) {
+      const double v = d->q[off + s];
+      if (v < 0) return fail(nullptr, MAM_ERR_INVALID_ARG, p + "negative weight");
+      if (v > 0) {
+        ++pos;
+        Q += v;
+      }
+    }
+    if (pos == 0)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  p + "measure " + std::to_string(m) + " has no positive weight");
+    if (m == 0) Q0 = Q;
+    if (std::isinf(d->gamma) && std::fabs(Q - Q0) > 1e-9 * Q0)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  p + "balanced problems (gamma = inf) need equal total masses; "
+                      "use a finite gamma for the unbalanced variant");
+    off += d->S[m];
+  }
+  return MAM_OK;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+namespace mam {
+
+// ----------------------------------------------------------- schedules
+
+static void build_sched_host(const mam_problem* h, long long c0, long long c1,
+                             int G, SchedHost& out) {
+  const long long n = c1 - c0;
+  out.col_begin = c0;
+  out.col_end = c1;
+  out.cta_seg_begin.assign(G + 1, 0);
+  out.segs.clear();
+  out.slot_begin.assign(h->Mtot, 0);
+  out.slot_end.assign(h->Mtot, 0);
+  std::vector<char> seen(h->Mtot, 0);
+  int nseg = 0;
+  int m = int(std::upper_bound(h->col_off.begin(), h->col_off.end(), c0) -
+              h->col_off.begin()) - 1;
+  for (int b = 0; b < G; ++b) {
+    out.cta_seg_begin[b] = nseg;
+    const long long cb = c0 + n * b / G, ce = c0 + n * (b + 1) / G;
+    long long c = cb;
+    while (c < ce) {
+      while (h->col_off[m + 1] <= c) ++m;
+      const long long e = std::min(ce, h->col_off[m + 1]);
+      out.segs.push_back(make_int4(m, int(c), int(e), nseg));
+      if (!seen[m]) {
+        seen[m] = 1;
+        out.slot_begin[m] = nseg;
+      }
+      out.slot_end[m] = nseg + 1;
+      ++nseg;
+      c = e;
+    }
+  }
+  out.cta_seg_begin[G] = nseg;
+}
+
+static void free_sched(mam_problem* h) {
+  for (void* p : h->sched_allocs) cudaFree(p);
+  h->sched_allocs.clear();
+  h->sched_d = nullptr;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+}
+
+static mam_status sched_alloc(mam_problem* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MAM_ERR_OOM, "cudaMalloc failed for the work schedule");
+  }
+  h->sched_allocs.push_back(*p);
+  return MAM_OK;
+}
+
+size_t column_smem_bytes(const mam_problem* h, int stages) {
+  return size_t(stages) * h->ld * (sizeof(float) + cost_elem_size(h->cost_dtype)) +
+         4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4);
+}
+
+mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
+  const int nvs[] = {1, 2, 3, 4, 5, 6, 8};
+  if (std::find(std::begin(nvs), std::end(nvs), c.vec) == std::end(nvs))
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "vec must be one of 1,2,3,4,5,6,8");
+  if (c.threads < 32 || c.threads % 32 || c.threads > column_max_threads(c.vec))
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "threads must be a multiple of 32 within the variant's limit (" +
+                    std::to_string(column_max_threads(c.vec)) + ")");
+  if ((long long)c.threads * c.vec * 4 < h->ld)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "threads * vec * 4 must cover the padded column (" +
+                    std::to_string(h->ld) + ")");
+  if (c.stages < 2 || c.stages > 4)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "stages must be 2..4");
+  if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "ctas_per_sm must be 0..32");
+  if (c.bisect_depth < 0 || c.bisect_depth > 30)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "bisect_depth must be 0..30");
+  if (column_smem_bytes(h, c.stages) > 232448)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "pipeline does not fit in shared memory; use fewer stages");
+  return MAM_OK;
+}
+
+mam_kernel_config default_config(const mam_problem* h) {
+  const int ld4 = h->ld / 4;
+  const int nvs[] = {4, 5, 3, 6, 2, 8, 1};
+  mam_kernel_config best{};
+  double best_score = -1;
+  for (int nv : nvs) {
+    const int nt = std::max(32, round_up((ld4 + nv - 1) / nv, 32));
+    if (nt > column_max_threads(nv)) continue;
+    const double util = double(ld4) / (double(nt) * nv);
+    const double score = util - 0.004 * std::abs(nv - 4);
+    if (score > best_score + 1e-12) {
+      best_score = score;
+      best.threads = nt;
+      best.vec = nv;
+    }
+  }
+  best.stages = 2;
+  best.ctas_per_sm = 0;
+  best.bisect_depth = 4;
+  return best;
+}
+
+mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
+  MAM_TRY(check_config(h, c));
+  const size_t smem = column_smem_bytes(h, c.stages);
+  for (int dg = 0; dg < 2; ++dg)
+    MAM_CUDA(set_column_smem(c.vec, h->cost_dtype, dg != 0, smem), "cudaFuncSetAttribute");
+  int occ = 0;
+  MAM_CUDA(column_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ),
+           "occupancy");
+  int occ2 = 0;
+  MAM_CUDA(column_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2),
+           "occupancy");
+  occ = std::min(occ, occ2);
+  if (occ < 1)
+    return fail(h, MAM_ERR_INVALID_ARG, "kernel configuration cannot be resident on an SM");
+  const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
+  long long max_cols = 0;
+  for (auto& r : h->index_sets) max_cols = std::max(max_cols, r.second - r.first);
+  long long G = (long long)per_sm * h->num_sms;
+  G = std::max(1LL, std::min(G, max_cols));
+
+  free_sched(h);
+  std::vector<SchedHost> hs(h->index_sets.size());
+  int max_slots = 0;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    build_sched_host(h, h->index_sets[i].first, h->index_sets[i].second, int(G), hs[i]);
+    max_slots = std::max(max_slots, int(hs[i].segs.size()));
+  }
+  std::vector<Sched> sd(hs.size());
+  for (size_t i = 0; i < hs.size(); ++i) {
+    void *a, *b, *c2, *d;
+    MAM_TRY(sched_alloc(h, &a, hs[i].cta_seg_begin.size() * sizeof(int)));
+    MAM_TRY(sched_alloc(h, &b, hs[i].segs.size() * sizeof(int4)));
+    MAM_TRY(sched_alloc(h, &c2, h->Mtot * sizeof(int)));
+    MAM_TRY(sched_alloc(h, &d, h->Mtot * sizeof(int)));
+    MAM_CUDA(cudaMemcpyAsync(a, hs[i].cta_seg_begin.data(), hs[i].cta_seg_begin.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream), "sched upload");
+    if (!hs[i].segs.empty())
+      MAM_CUDA(cudaMemcpyAsync(b, hs[i].segs.data(), hs[i].segs.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream), "sched upload");
+    MAM_CUDA(cudaMemcpyAsync(c2, hs[i].slot_begin.data(), h->Mtot * sizeof(int), cudaMemcpyHostToDevice, h->stream), "sched upload");
+    MAM_CUDA(cudaMemcpyAsync(d, hs[i].slot_end.data(), h->Mtot * sizeof(int), cudaMemcpyHostToDevice, h->stream), "sched upload");
+    sd[i].cta_seg_begin = static_cast<int*>(a);
+    sd[i].segs = static_cast<int4*>(b);
+    sd[i].slot_begin = static_cast<int*>(c2);
+    sd[i].slot_end = static_cast<int*>(d);
+    sd[i].col_begin = hs[i].col_begin;
+    sd[i].col_end = hs[i].col_end;
+  }
+  void* sp;
+  MAM_TRY(sched_alloc(h, &sp, sd.size() * sizeof(Sched)));
+  MAM_CUDA(cudaMemcpyAsync(sp, sd.data(), sd.size() * sizeof(Sched), cudaMemcpyHostToDevice, h->stream), "sched upload");
+  h->sched_d = static_cast<Sched*>(sp);
+  if (max_slots > h->max_slots) {
+    if (h->partials) {
+      cudaFree(h->partials);
+      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)h->partials));
+      h->partials = nullptr;
+    }
+    MAM_TRY(dalloc(h, &h->partials, size_t(max_slots) * h->ld, "partial row sums"));
+    h->max_slots = max_slots;
+  }
+  h->cfg = c;
+  h->grid = int(G);
+  h->smem = smem;
+  MAM_CUDA(cudaStreamSynchronize(h->stream), "schedule upload");
+  return MAM_OK;
+}
+
+// ------------------------------------------------------------ iteration
+
+ColArgs col_args(const mam_problem* h) {
+  ColArgs a{};
+  a.theta = h->theta;
+  a.cost = h->cost;
+  a.q = h->q;
+  a.lam = h->lam;
+  a.delta = h->delta;
+  a.t = h->t;
+  a.meas_prob = h->meas_prob;
+  a.rho = h->rho_m;
+  a.inv_rho = h->irho_m;
+  a.partials = h->partials;
+  a.sched = h->sched_d;
+  a.bundle_cur = h->nb > 1 ? h->bundle_cur : nullptr;
+  a.diag_wc = h->diag_wc;
+  a.diag_lb = h->diag_lb;
+  a.diag_res = h->diag_res;
+  a.passes = h->passes;
+  a.err = h->err_d;
+  a.R = h->R;
+  a.ld = h->ld;
+  a.stages = h->cfg.stages;
+  a.bisect_depth = h->cfg.bisect_depth;
+  return a;
+}
+
+AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
+  AvgArgs a{};
+  a.P = h->P;
+  a.R = h->R;
+  a.ld = h->ld;
+  a.prob_meas = h->prob_meas_d;
+  a.S = h->S_d;
+  a.a = h->a_d;
+  a.rho = h->rho_d;
+  a.gamma = h->gamma_d;
+  a.partials = h->partials;
+  a.sched = h->sched_d;
+  a.bundle_cur = h->nb > 1 ? h->bundle_cur : nullptr;
+  a.bundle_prev = h->nb > 1 ? h->bundle_prev : nullptr;
+  a.reduce = reduce;
+  a.diag = diag;
+  a.pm = h->pm;
+  a.p = h->p;
+  a.delta = h->delta;
+  a.phat = h->phat;
+  a.t = h->t;
+  a.blk = h->blk;
+  a.counter = h->counter;
+  a.stat = h->stat;
+  a.nb = h->nb;
+  a.bundle_cum = h->bundle_cum_d;
+  a.seed = h->seed;
+  a.iter = h->iter_d;
+  a.bundle_next = h->bundle_cur;
+  return a;
+}
+
+int avg_blocks(const mam_problem* h) { return (h->R + 255) / 256; }
+
+static mam_status prof_event(mam_problem* h, cudaEvent_t* ev) {
+  if (h->prof_used >= h->prof_events.size()) {
+    cudaEvent_t e;
+    MAM_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    h->prof_events.push_back(e);
+  }
+  *ev = h->prof_events[h->prof_used++];
+  return MAM_OK;
+}
+
+mam_status launch_iteration(mam_problem* h, bool diag) {
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (h->profiling) {
+    for (auto& e : ev) MAM_TRY(prof_event(h, &e));
+    MAM_CUDA(cudaEventRecord(ev[0], h->stream), "cudaEventRecord");
+  }
+  if (diag && h->nb > 1) {
+    // Lower bound of every measure for the same v^k the column step uses.
+    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta, h->t, h->meas_prob,
+                       h->rho_m, h->col_meas, h->T, h->R, h->ld, h->diag_lb,
+                       h->stream),
+             "lower-bound kernel");
+  }
+  const ColArgs ca = col_args(h);
+  MAM_CUDA(launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
+                         h->smem, h->stream, ca),
+           "column kernel launch");
+  if (h->profiling) MAM_CUDA(cudaEventRecord(ev[1], h->stream), "cudaEventRecord");
+  const AvgArgs aa = avg_args(h, 1, diag ? 1 : 0);
+  MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
+  if (h->profiling) MAM_CUDA(cudaEventRecord(ev[2], h->stream), "cudaEventRecord");
+  return MAM_OK;
+}
+
+static mam_status ensure_graph(mam_problem* h) {
+  if (h->graph) return MAM_OK;
+  cudaGraph_t g = nullptr;
+  MAM_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+           "cudaStreamBeginCapture");
+  mam_status st = MAM_OK;
+  for (int i = 0; i < kGraphIters && st == MAM_OK; ++i) st = launch_iteration(h, false);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (st != MAM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return cuda_fail(h, e, "cudaGraphInstantiate");
+  }
+  return MAM_OK;
+}
+
+mam_status run_iterations(mam_problem* h, int n, bool diag_last) {
+  if (n <= 0) return MAM_OK;
+  const bool every = h->diag_mode == MAM_DIAG_EVERY;
+  const int nd = every ? n : (diag_last ? 1 : 0);
+  int plain = n - nd;
+  if (h->profiling) {  // per-kernel events need individual launches
+    while (plain-- > 0) MAM_TRY(launch_iteration(h, false));
+    plain = 0;
+  }
+  if (plain >= kGraphIters) MAM_TRY(ensure_graph(h));
+  while (plain >= kGraphIters) {
+    MAM_CUDA(cudaGraphLaunch(h->graph, h->stream), "cudaGraphLaunch");
+    plain -= kGraphIters;
+  }
+  while (plain-- > 0) MAM_TRY(launch_iteration(h, false));
+  for (int i = 0; i < nd; ++i) MAM_TRY(launch_iteration(h, true));
+  h->iter += n;
+  if (nd > 0) h->diag_iter = h->iter;
+  return MAM_OK;
+}
+
+mam_status check_device_error(mam_problem* h) {
+  int e = 0;
+  MAM_CUDA(cudaMemcpy(&e, h->err_d, sizeof(int), cudaMemcpyDeviceToHost),
+           "error word read");
+  if (e != 0)
+    return fail(h, MAM_ERR_TIMEOUT,
+                "a device-side wait exceeded its bound (the iterate is invalid)");
+  return MAM_OK;
+}
+
+mam_status sync(mam_problem* h) {
+  MAM_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  return check_device_error(h);
+}
+
+// ------------------------------------------------------------ creation
+
+mam_status reset_state(mam_problem* h) {
+  MAM_CUDA(launch_init_theta(h->theta, h->lam, h->q64, h->T, h->R, h->ld,
+                             h->theta0_mode, h->stream),
+           "init kernel");
+  MAM_CUDA(launch_rowsum(h->theta, h->col_off_d, h->Mtot, h->R, h->ld, h->pm,
+                         h->stream),
+           "rowsum kernel");
+  MAM_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * h->P * h->R, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->phat, 0, sizeof(double) * size_t(h->Mtot) * h->R, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->diag_wc, 0, sizeof(float) * h->T, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->diag_lb, 0, sizeof(float) * h->T, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->diag_res, 0, sizeof(float) * h->T, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->iter_d, 0, sizeof(long long), h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->bundle_cur, 0, sizeof(int), h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->bundle_prev, 0, sizeof(int), h->stream), "memset");
+  std::vector<double> ones(h->P, 1.0);
+  MAM_TRY(upload(h, h->t, ones.data(), ones.size()));
+  MAM_CUDA(cudaMemsetAsync(h->stat, 0, sizeof(double) * 4 * h->P, h->stream), "memset");
+  const AvgArgs aa = avg_args(h, 0, 0);
+  MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
+  h->iter = 0;
+  h->diag_iter = -1;
+  return sync(h);
+}
+
+static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
+  if (!out) return fail(nullptr, MAM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !descs) return fail(nullptr, MAM_ERR_INVALID_ARG, "need at least one problem");
+  for (int i = 0; i < n; ++i) MAM_TRY(validate(&descs[i], i));
+  for (int i = 1; i < n; ++i) {
+    if (descs[i].R != descs[0].R || descs[i].dim != descs[0].dim ||
+        descs[i].cost_dtype != descs[0].cost_dtype ||
+        descs[i].diag_mode != descs[0].diag_mode ||
+        descs[i].theta0_mode != descs[0].theta0_mode)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  "batched problems must share R, dim, cost_dtype, diag_mode and theta0_mode");
+  }
+  if (n > 1)
+    for (int i = 0; i < n; ++i)
+      if (descs[i].n_bundles > 1)
+        return fail(nullptr, MAM_ERR_INVALID_ARG,
+                    "batched problems must be deterministic (n_bundles <= 1)");
+
+  mam_problem* h = new mam_problem();
+  auto bail = [&](mam_status s) {
+    if (h->failed || s != MAM_OK) g_last_error = h->err;
+    mam_destroy(h);
+    return s;
+  };
+  const mam_desc& d0 = descs[0];
+  h->P = n;
+  h->R = d0.R;
+  h->dim = d0.dim;
+  h->ld = round_up(d0.R, 8);
+  h->cost_dtype = d0.cost_dtype;
+  h->theta0_mode = d0.theta0_mode;
+  h->diag_mode = d0.diag_mode;
+  h->nb = (n == 1 && d0.n_bundles > 1) ? d0.n_bundles : 1;
+  h->seed = d0.seed;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "device query"));
+  if (d0.stream) {
+    h->stream = static_cast<cudaStream_t>(d0.stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaStreamCreate"));
+    h->own_stream = true;
+  }
+
+  // Host layout: pruning (Section 4.3) and the per-measure constants.
+  h->prob_meas.push_back(0);
+  h->prob_cols.push_back(0);
+  h->col_off.push_back(0);
+  h->unpruned_off.push_back(0);
+  std::vector<double> q64;
+  std::vector<float> q32;
+  std::vector<int> col_meas;
+  std::vector<double> alpha_m;
+  long long uoff_global = 0;
+  for (int i = 0; i < n; ++i) {
+    const mam_desc& d = descs[i];
+    double inv_sum = 0;
+    std::vector<int> Sp(d.M);
+    long long uoff = 0;
+    for (int m = 0; m < d.M; ++m) {
+      int cnt = 0;
+      for (int s = 0; s < d.S[m]; ++s) cnt += d.q[uoff + s] > 0;
+      Sp[m] = cnt;
+      inv_sum += 1.0 / cnt;
+      uoff += d.S[m];
+    }
+    uoff = 0;
+    double Qa = 0;
+    for (int m = 0; m < d.M; ++m) {
+      const int gm = h->Mtot + m;
+      h->S.push_back(Sp[m]);
+      h->S_unpruned.push_back(d.S[m]);
+      const double am = (1.0 / Sp[m]) / inv_sum;
+      h->a.push_back(am);
+      h->meas_prob_h.push_back(i);
+      alpha_m.push_back(d.alpha[m]);
+      double Q = 0;
+      for (int s = 0; s < d.S[m]; ++s) {
+        const double v = d.q[uoff + s];
+        if (v > 0) {
+          q64.push_back(v);
+          q32.push_back(float(v));
+          col_meas.push_back(gm);
+          h->keep.push_back(uoff_global + uoff + s);
+          Q += v;
+        }
+      }
+      Qa += am * Q;
+      h->col_off.push_back(h->col_off.back() + Sp[m]);
+      h->unpruned_off.push_back(h->unpruned_off.back() + d.S[m]);
+      uoff += d.S[m];
+    }
+    uoff_global += uoff;
+    h->Mtot += d.M;
+    h->prob_meas.push_back(h->Mtot);
+    h->prob_cols.push_back(h->col_off.back());
+    h->rho.push_back(d.rho);
+    h->gamma.push_back(d.gamma);
+    h->Qa.push_back(Qa);
+  }
+  h->T = h->col_off.back();
+  if (h->T >= (1LL << 31) - 1)
+    return bail(fail(h, MAM_ERR_INVALID_ARG, "too many kept columns (>= 2^31)"));
+
+  // Index sets: all columns, or the bundles of Remark 2 (contiguous measures).
+  if (h->nb > 1) {
+    const int M = d0.M;
+    double tot = 0;
+    std::vector<double> beta(h->nb);
+    for (int b = 0; b < h->nb; ++b) {
+      const int m0 = int((long long)b * M / h->nb), m1 = int((long long)(b + 1) * M / h->nb);
+      double s = 0;
+      for (int m = m0; m < m1; ++m) s += d0.alpha[m];
+      beta[b] = s;
+      tot += s;
+      h->index_sets.push_back({h->col_off[m0], h->col_off[m1]});
+    }
+    if (!(tot > 0))
+      return bail(fail(h, MAM_ERR_INVALID_ARG, "randomized MAM needs sum(alpha) > 0"));
+    double acc = 0;
+    for (int b = 0; b < h->nb; ++b) {
+      acc += beta[b] / tot;
+      h->bundle_cum.push_back(acc);
+    }
+  } else {
+    h->index_sets.push_back({0, h->T});
+  }
+
+  // Device buffers.
+  const size_t Tld = size_t(h->T) * h->ld;
+  const size_t MR = size_t(h->Mtot) * h->R;
+  mam_status s = MAM_OK;
+#define ALLOC(ptr, count, what) \
+  if ((s = dalloc(h, &(ptr), (count), (what))) != MAM_OK) return bail(s)
+  ALLOC(h->theta, Tld, "plans theta");
+  void* costp = nullptr;
+  {
+    char* cp = nullptr;
+    ALLOC(cp, Tld * cost_elem_size(h->cost_dtype), "costs");
+    costp = cp;
+  }
+  h->cost = costp;
+  ALLOC(h->q, size_t(h->T), "weights");
+  ALLOC(h->q64, size_t(h->T), "weights (fp64)");
+  ALLOC(h->lam, size_t(h->T), "thresholds");
+  ALLOC(h->pm, MR, "marginals");
+  ALLOC(h->delta, MR, "shifts");
+  ALLOC(h->phat, MR, "pi-hat marginals");
+  ALLOC(h->p, size_t(h->P) * h->R, "barycenters");
+  ALLOC(h->t, size_t(h->P), "t");
+  ALLOC(h->blk, size_t(h->P) * avg_blocks(h) * 4, "block sums");
+  ALLOC(h->counter, size_t(h->P), "counters");
+  ALLOC(h->stat, size_t(h->P) * 4, "statistics");
+  ALLOC(h->diag_wc, size_t(h->T), "diagnostics");
+  ALLOC(h->diag_lb, size_t(h->T), "diagnostics");
+  ALLOC(h->diag_res, size_t(h->T), "diagnostics");
+  ALLOC(h->diag_out, size_t(h->P) * 3, "diagnostic sums");
+  ALLOC(h->passes, 1, "pass counter");
+  ALLOC(h->err_d, 1, "error word");
+  ALLOC(h->meas_prob, size_t(h->Mtot), "measure table");
+  ALLOC(h->rho_m, size_t(h->Mtot), "rho table");
+  ALLOC(h->irho_m, size_t(h->Mtot), "rho table");
+  ALLOC(h->a_d, size_t(h->Mtot), "weights a");
+  ALLOC(h->alpha_d, size_t(h->Mtot), "alpha");
+  ALLOC(h->S_d, size_t(h->Mtot), "sizes");
+  ALLOC(h->prob_meas_d, size_t(h->P) + 1, "problem table");
+  ALLOC(h->rho_d, size_t(h->P), "rho");
+  ALLOC(h->gamma_d, size_t(h->P), "gamma");
+  ALLOC(h->col_off_d, size_t(h->Mtot) + 1, "column offsets");
+  ALLOC(h->prob_cols_d, size_t(h->P) + 1, "problem columns");
+  ALLOC(h->col_meas, size_t(h->T), "column table");
+  ALLOC(h->bundle_cum_d, std::max<size_t>(1, h->bundle_cum.size()), "bundle table");
+  ALLOC(h->iter_d, 1, "iteration counter");
+  ALLOC(h->bundle_cur, 1, "bundle");
+  ALLOC(h->bundle_prev, 1, "bundle");
+#undef ALLOC
+
+  std::vector<float> rho_m(h->Mtot), irho_m(h->Mtot);
+  for (int m = 0; m < h->Mtot; ++m) {
+    rho_m[m] = float(h->rho[h->meas_prob_h[m]]);
+    irho_m[m] = float(1.0 / h->rho[h->meas_prob_h[m]]);
+  }
+  if ((s = upload(h, h->q, q32.data(), q32.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->q64, q64.data(), q64.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->meas_prob, h->meas_prob_h.data(), h->meas_prob_h.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->rho_m, rho_m.data(), rho_m.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->irho_m, irho_m.data(), irho_m.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->a_d, h->a.data(), h->a.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->alpha_d, alpha_m.data(), alpha_m.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->S_d, h->S.data(), h->S.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->prob_meas_d, h->prob_meas.data(), h->prob_meas.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->rho_d, h->rho.data(), h->rho.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->gamma_d, h->gamma.data(), h->gamma.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->col_off_d, h->col_off.data(), h->col_off.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->prob_cols_d, h->prob_cols.data(), h->prob_cols.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->col_meas, col_meas.data(), col_meas.size())) != MAM_OK) return bail(s);
+  if (!h->bundle_cum.empty() &&
+      (s = upload(h, h->bundle_cum_d, h->bundle_cum.data(), h->bundle_cum.size())) != MAM_OK)
+    return bail(s);
+  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * h->P, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->passes, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+
+  // Keep the kept support points and the barycenter points (backward pass).
+  for (int i = 0; i < n; ++i) {
+    const mam_desc& d = descs[i];
+    h->xi_h.insert(h->xi_h.end(), d.xi, d.xi + size_t(d.R) * d.dim);
+  }
+  h->has_gen_cost = false;
+  for (int i = 0; i < n; ++i) h->has_gen_cost |= descs[i].cost != nullptr;
+
+  // Costs (eq. HugeLP), built on the device problem by problem.
+  {
+    double* xi_d = nullptr;
+    double* zeta_d = nullptr;
+    double* gen_d = nullptr;
+    auto tmp_free = [&]() {
+      if (xi_d) cudaFree(xi_d);
+      if (zeta_d) cudaFree(zeta_d);
+      if (gen_d) cudaFree(gen_d);
+    };
+    long long uoff_g = 0;
+    for (int i = 0; i < n && s == MAM_OK; ++i) {
+      const mam_desc& d = descs[i];
+      const long long c0 = h->prob_cols[i], c1 = h->prob_cols[i + 1];
+      long long utot = 0;
+      for (int m = 0; m < d.M; ++m) utot += d.S[m];
+      if (!xi_d) {
+        if (cudaMalloc(&xi_d, sizeof(double) * size_t(d.R) * d.dim) != cudaSuccess) {
+          cudaGetLastError();
+          s = fail(h, MAM_ERR_OOM, "cudaMalloc failed for xi");
+          break;
+        }
+      }
+      e = cudaMemcpy(xi_d, d.xi, sizeof(double) * size_t(d.R) * d.dim, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) { s = cuda_fail(h, e, "xi upload"); break; }
+      if (!d.cost) {
+        std::vector<double> zk(size_t(c1 - c0) * d.dim);
+        for (long long c = c0; c < c1; ++c)
+          for (int k = 0; k < d.dim; ++k)
+            zk[size_t(c - c0) * d.dim + k] = d.zeta[size_t(h->keep[c] - uoff_g) * d.dim + k];
+        h->zeta_kept.insert(h->zeta_kept.end(), zk.begin(), zk.end());
+        if (zeta_d) cudaFree(zeta_d);
+        zeta_d = nullptr;
+        if (cudaMalloc(&zeta_d, sizeof(double) * std::max<size_t>(1, zk.size())) != cudaSuccess) {
+          cudaGetLastError();
+          s = fail(h, MAM_ERR_OOM, "cudaMalloc failed for zeta");
+          break;
+        }
+        e = cudaMemcpy(zeta_d, zk.data(), sizeof(double) * zk.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { s = cuda_fail(h, e, "zeta upload"); break; }
+        e = launch_build_cost(h->cost_dtype, h->cost, xi_d, zeta_d, nullptr,
+                              h->col_meas, h->alpha_d, c0, c1 - c0, h->R, h->ld,
+                              h->dim, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { s = cuda_fail(h, e, "cost kernel"); break; }
+      } else {
+        if (d.zeta) {
+          for (long long c = c0; c < c1; ++c)
+            for (int k = 0; k < d.dim; ++k)
+              h->zeta_kept.push_back(d.zeta[size_t(h->keep[c] - uoff_g) * d.dim + k]);
+        }
+        const long long chunk = std::max<long long>(1, (64LL << 20) / (8LL * d.R));
+        if (!gen_d) {
+          if (cudaMalloc(&gen_d, sizeof(double) * size_t(chunk) * d.R) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(h, MAM_ERR_OOM, "cudaMalloc failed for the cost staging buffer");
+            break;
+          }
+        }
+        std::vector<double> buf;
+        for (long long cb = c0; cb < c1 && s == MAM_OK; cb += chunk) {
+          const long long ce = std::min(c1, cb + chunk);
+          buf.resize(size_t(ce - cb) * d.R);
+          for (long long c = cb; c < ce; ++c)
+            std::memcpy(&buf[size_t(c - cb) * d.R],
+                        d.cost + size_t(h->keep[c] - uoff_g) * d.R, sizeof(double) * d.R);
+          e = cudaMemcpy(gen_d, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice);
+          if (e == cudaSuccess)
+            e = launch_build_cost(h->cost_dtype, h->cost, xi_d, nullptr, gen_d, h->col_meas,
+                                  h->alpha_d, cb, ce - cb, h->R, h->ld, h->dim, h->stream);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+          if (e != cudaSuccess) s = cuda_fail(h, e, "cost kernel");
+        }
+      }
+      uoff_g += utot;
+    }
+    tmp_free();
+    if (s != MAM_OK) return bail(s);
+  }
+
+  if ((s = apply_config(h, default_config(h))) != MAM_OK) return bail(s);
+  if ((s = reset_state(h)) != MAM_OK) return bail(s);
+  *out = h;
+  return MAM_OK;
+}
+
+}  // namespace mam
+
+// ================================================================ C ABI
+
+extern "C" {
+
+mam_status mam_create(const mam_desc* desc, mam_problem** out) {
+  return create_impl(1, desc, out);
+}
+
+mam_status mam_batch_create(int32_t n, const mam_desc* descs, mam_problem** out) {
+  return create_impl(n, descs, out);
+}
+
+#define MAM_CHECK_HANDLE(h)                                                \
+  do {                                                                     \
+    if (!(h)) return fail(nullptr, MAM_ERR_INVALID_ARG, "null handle");    \
+    if ((h)->failed) return MAM_ERR_STATE;                                 \
+  } while (0)
+
+mam_status mam_step(mam_problem* h, int32_t n_iters) {
+  MAM_CHECK_HANDLE(h);
+  if (n_iters < 0) return fail(h, MAM_ERR_INVALID_ARG, "n_iters must be >= 0");
+  return run_iterations(h, n_iters, h->diag_mode == MAM_DIAG_LAST);
+}
+
+static mam_status objective_all(mam_problem* h, std::vector<mam_objective_t>& out) {
+  MAM_TRY(sync(h));
+  MAM_CUDA(launch_diag_reduce(h->diag_wc, h->diag_lb, h->diag_res, h->prob_cols_d,
+                              h->sched_d, h->nb > 1 ? h->bundle_prev : nullptr, h->P,
+                              h->diag_out, h->stream),
+           "diagnostic reduction");
+  std::vector<double> sums(size_t(h->P) * 3), stat(size_t(h->P) * 4), t(h->P);
+  unsigned long long passes = 0;
+  MAM_CUDA(cudaMemcpyAsync(sums.data(), h->diag_out, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_CUDA(cudaMemcpyAsync(stat.data(), h->stat, sizeof(double) * stat.size(), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_CUDA(cudaMemcpyAsync(&passes, h->passes, sizeof(passes), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_CUDA(cudaMemcpyAsync(t.data(), h->t, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_TRY(sync(h));
+  out.resize(h->P);
+  for (int i = 0; i < h->P; ++i) {
+    mam_objective_t& o = out[i];
+    o.w_hat = sums[3 * i];
+    o.lower_bound = sums[3 * i + 1];
+    o.fp_resid = std::sqrt(sums[3 * i + 2]);
+    o.dist_pihat = stat[4 * i + 1];
+    o.f_unbal = o.w_hat + (std::isinf(h->gamma[i]) ? 0.0 : h->gamma[i] * o.dist_pihat);
+    o.dp_norm = stat[4 * i + 2];
+    o.t = stat[4 * i + 3];
+    o.dist_theta = stat[4 * i];
+    o.t_next = t[i];
+    o.iter = h->diag_iter;
+    o.newton_passes = (int64_t)passes;
+  }
+  return MAM_OK;
+}
+
+mam_status mam_objective(mam_problem* h, int32_t index, mam_objective_t* out) {
+  MAM_CHECK_HANDLE(h);
+  if (!out || index < 0 || index >= h->P)
+    return fail(h, MAM_ERR_INVALID_ARG, "bad objective index or output");
+  std::vector<mam_objective_t> all;
+  MAM_TRY(objective_all(h, all));
+  *out = all[index];
+  const double v[] = {out->w_hat, out->lower_bound, out->fp_resid, out->dist_pihat,
+                      out->dist_theta, out->t};
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(h, MAM_ERR_NONFINITE, "non-finite diagnostic");
+  return MAM_OK;
+}
+
+mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol, double w_ref,
+                     int32_t check_every, int32_t* iters_done, double* gap_out) {
+  MAM_CHECK_HANDLE(h);
+  if (max_iters < 0 || check_every < 1 || !(gap_tol >= 0))
+    return fail(h, MAM_ERR_INVALID_ARG, "bad solve arguments");
+  int done = 0;
+  double gap = INFINITY;
+  std::vector<mam_objective_t> all;
+  while (done < max_iters) {
+    const int n = std::min<int>(check_every, max_iters - done);
+    MAM_TRY(run_iterations(h, n, true));
+    done += n;
+    MAM_TRY(objective_all(h, all));
+    gap = 0;
+    for (int i = 0; i < h->P; ++i) {
+      const mam_objective_t& o = all[i];
+      const double ref = w_ref > 0 ? w_ref : o.lower_bound;
+      double g = std::fabs(o.f_unbal - ref) / std::max(std::fabs(ref), 1e-300);
+      if (std::isinf(h->gamma[i])) g = std::max(g, o.dist_pihat / h->Qa[i]);
+      if (!std::isfinite(g)) {
+        if (iters_done) *iters_done = done;
+        return fail(h, MAM_ERR_NONFINITE, "non-finite gap");
+      }
+      gap = std::max(gap, g);
+    }
+    if (gap <= gap_tol) break;
+  }
+  if (iters_done) *iters_done = done;
+  if (gap_out) *gap_out = gap;
+  return MAM_OK;
+}
+
+mam_status mam_get_barycenter(mam_problem* h, double* p_out, int32_t device_ptr) {
+  MAM_CHECK_HANDLE(h);
+  if (!p_out) return fail(h, MAM_ERR_INVALID_ARG, "p_out is NULL");
+  MAM_CUDA(cudaMemcpyAsync(p_out, h->p, sizeof(double) * h->P * h->R,
+                           device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           h->stream),
+           "barycenter copy");
+  return sync(h);
+}
+
+mam_status mam_get_marginals(mam_problem* h, double* pm_out, int32_t device_ptr) {
+  MAM_CHECK_HANDLE(h);
+  if (!pm_out) return fail(h, MAM_ERR_INVALID_ARG, "pm_out is NULL");
+  MAM_CUDA(cudaMemcpyAsync(pm_out, h->pm, sizeof(double) * size_t(h->Mtot) * h->R,
+                           device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           h->stream),
+           "marginal copy");
+  return sync(h);
+}
+
+mam_status mam_get_theta(mam_problem* h, float* theta_out) {
+  MAM_CHECK_HANDLE(h);
+  if (!theta_out) return fail(h, MAM_ERR_INVALID_ARG, "theta_out is NULL");
+  MAM_CUDA(cudaMemcpy2DAsync(theta_out, sizeof(float) * h->R, h->theta,
+                             sizeof(float) * h->ld, sizeof(float) * h->R, h->T,
+                             cudaMemcpyDeviceToHost, h->stream),
+           "theta copy");
+  return sync(h);
+}
+
+mam_status mam_get_sizes(const mam_problem* h, int32_t* n_problems, int32_t* n_measures,
+                         int32_t* R, int64_t* T, int32_t* ld) {
+  if (!h) return fail(nullptr, MAM_ERR_INVALID_ARG, "null handle");
+  if (n_problems) *n_problems = h->P;
+  if (n_measures) *n_measures = h->Mtot;
+  if (R) *R = h->R;
+  if (T) *T = h->T;
+  if (ld) *ld = h->ld;
+  return MAM_OK;
+}
+
+mam_status mam_get_pruned_sizes(const mam_problem* h, int32_t* S_out) {
+  if (!h) return fail(nullptr, MAM_ERR_INVALID_ARG, "null handle");
+  if (!S_out) return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "S_out is NULL");
+  for (int m = 0; m < h->Mtot; ++m) S_out[m] = h->S[m];
+  return MAM_OK;
+}
+
+// ------------------------------------------------------------ checkpoints
+
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  int64_t T, iter, diag_iter;
+  int32_t P, Mtot, R, ld;
+  int32_t bundle_cur, bundle_prev, pad0, pad1;
+};
+constexpr uint64_t kStateMagic = 0x314554415453414dull;  // "MASTATE1"
+
+struct Piece {
+  void* dev;
+  size_t bytes;
+};
+
+std::vector<Piece> state_pieces(mam_problem* h) {
+  const size_t MR = size_t(h->Mtot) * h->R;
+  return {{h->theta, sizeof(float) * size_t(h->T) * h->ld},
+          {h->lam, sizeof(float) * size_t(h->T)},
+          {h->pm, sizeof(double) * MR},
+          {h->p, sizeof(double) * size_t(h->P) * h->R},
+          {h->delta, sizeof(double) * MR},
+          {h->phat, sizeof(double) * MR},
+          {h->t, sizeof(double) * h->P},
+          {h->stat, sizeof(double) * 4 * h->P},
+          {h->diag_wc, sizeof(float) * size_t(h->T)},
+          {h->diag_lb, sizeof(float) * size_t(h->T)},
+          {h->diag_res, sizeof(float) * size_t(h->T)},
+          {h->passes, sizeof(unsigned long long)},
+          {h->iter_d, sizeof(long long)}};
+}
+}  // namespace
+
+mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes) {
+  MAM_CHECK_HANDLE(h);
+  if (!bytes) return fail(h, MAM_ERR_INVALID_ARG, "bytes is NULL");
+  const auto pieces = state_pieces(h);
+  size_t need = sizeof(StateHeader);
+  for (auto& p : pieces) need += p.bytes;
+  if (!buf) {
+    *bytes = need;
+    return MAM_OK;
+  }
+  if (*bytes < need) return fail(h, MAM_ERR_INVALID_ARG, "state buffer too small");
+  MAM_TRY(sync(h));
+  StateHeader hd{};
+  hd.magic = kStateMagic;
+  hd.T = h->T;
+  hd.iter = h->iter;
+  hd.diag_iter = h->diag_iter;
+  hd.P = h->P;
+  hd.Mtot = h->Mtot;
+  hd.R = h->R;
+  hd.ld = h->ld;
+  MAM_CUDA(cudaMemcpy(&hd.bundle_cur, h->bundle_cur, sizeof(int), cudaMemcpyDeviceToHost), "state");
+  MAM_CUDA(cudaMemcpy(&hd.bundle_prev, h->bundle_prev, sizeof(int), cudaMemcpyDeviceToHost), "state");
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  for (auto& p : pieces) {
+    MAM_CUDA(cudaMemcpy(out + off, p.dev, p.bytes, cudaMemcpyDeviceToHost), "state");
+    off += p.bytes;
+  }
+  *bytes = need;
+  return MAM_OK;
+}
+
+mam_status mam_set_state(mam_problem* h, const void* buf, size_t bytes) {
+  MAM_CHECK_HANDLE(h);
+  if (!buf) return fail(h, MAM_ERR_INVALID_ARG, "buf is NULL");
+  const auto pieces = state_pieces(h);
+  size_t need = sizeof(StateHeader);
+  for (auto& p : pieces) need += p.bytes;
+  StateHeader hd;
+  if (bytes < need) return fail(h, MAM_ERR_INVALID_ARG, "state buffer too small");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.T != h->T || hd.P != h->P || hd.Mtot != h->Mtot ||
+      hd.R != h->R || hd.ld != h->ld)
+    return fail(h, MAM_ERR_INVALID_ARG, "state does not belong to this problem");
+  MAM_TRY(sync(h));
+  const char* in = static_cast<const char*>(buf);
+  size_t off = sizeof(hd);
+  for (auto& p : pieces) {
+    MAM_CUDA(cudaMemcpy(p.dev, in + off, p.bytes, cudaMemcpyHostToDevice), "state");
+    off += p.bytes;
+  }
+  MAM_CUDA(cudaMemcpy(h->bundle_cur, &hd.bundle_cur, sizeof(int), cudaMemcpyHostToDevice), "state");
+  MAM_CUDA(cudaMemcpy(h->bundle_prev, &hd.bundle_prev, sizeof(int), cudaMemcpyHostToDevice), "state");
+  h->iter = hd.iter;
+  h->diag_iter = hd.diag_iter;
+  return MAM_OK;
+}
+
+// ------------------------------------------------------------ config
+
+mam_status mam_get_config(const mam_problem* h, mam_kernel_config* cfg) {
+  if (!h || !cfg) return fail(nullptr, MAM_ERR_INVALID_ARG, "null argument");
+  *cfg = h->cfg;
+  return MAM_OK;
+}
+
+mam_status mam_set_config(mam_problem* h, const mam_kernel_config* cfg) {
+  MAM_CHECK_HANDLE(h);
+  if (!cfg) return fail(h, MAM_ERR_INVALID_ARG, "cfg is NULL");
+  MAM_TRY(sync(h));
+  const mam_kernel_config old = h->cfg;
+  mam_status s = apply_config(h, *cfg);
+  if (s != MAM_OK && s != MAM_ERR_CUDA) {
+    const std::string msg = h->err;
+    apply_config(h, old);
+    h->err = msg;
+  }
+  return s;
+}
+
+mam_status mam_profile_enable(mam_problem* h, int32_t enable) {
+  MAM_CHECK_HANDLE(h);
+  MAM_TRY(sync(h));
+  h->profiling = enable != 0;
+  h->prof_used = 0;
+  return MAM_OK;
+}
+
+mam_status mam_profile_read(mam_problem* h, double* column_ms, double* average_ms,
+                            int64_t* launches) {
+  MAM_CHECK_HANDLE(h);
+  MAM_TRY(sync(h));
+  double c = 0, a = 0;
+  const size_t n = h->prof_used / 3;
+  for (size_t i = 0; i < n; ++i) {
+    float x = 0, y = 0;
+    MAM_CUDA(cudaEventElapsedTime(&x, h->prof_events[3 * i], h->prof_events[3 * i + 1]), "cudaEventElapsedTime");
+    MAM_CUDA(cudaEventElapsedTime(&y, h->prof_events[3 * i + 1], h->prof_events[3 * i + 2]), "cudaEventElapsedTime");
+    c += x;
+    a += y;
+  }
+  if (column_ms) *column_ms = c;
+  if (average_ms) *average_ms = a;
+  if (launches) *launches = int64_t(n);
+  h->prof_used = 0;
+  return MAM_OK;
+}
+
+const char* mam_last_error(const mam_problem* h) {
+  if (h) return h->err.c_str();
+  return g_last_error.c_str();
+}
+
+void mam_destroy(mam_problem* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_sched(h);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  free_backward(h);
+  for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

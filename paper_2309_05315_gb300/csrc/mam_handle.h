@@ -1,0 +1,154 @@
+// The library-owned problem handle (opaque behind include/mam.h) and the
+// host helpers shared by libmam's translation units.
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mam.h"
+#include "mam_internal.h"
+
+namespace mam {
+
+constexpr int kGraphIters = 10;  // iterations per captured CUDA graph
+constexpr int kMaxR = 12288;     // largest column a CTA covers (threads*vec*4)
+
+struct SchedHost {
+  std::vector<int> cta_seg_begin;
+  std::vector<int4> segs;
+  std::vector<int> slot_begin, slot_end;
+  long long col_begin = 0, col_end = 0;
+};
+
+struct BackwardState;  // mam_backward.cu
+
+}  // namespace mam
+
+struct mam_problem {
+  std::string err;
+  bool failed = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, num_sms = 0;
+
+  // sizes and modes
+  int P = 1, Mtot = 0, R = 0, ld = 0, dim = 0;
+  long long T = 0;
+  int cost_dtype = 0, theta0_mode = 0, diag_mode = 0;
+  int nb = 1;
+  unsigned long long seed = 0;
+  bool has_gen_cost = false;
+
+  // host tables
+  std::vector<int> prob_meas;           // [P+1]
+  std::vector<long long> prob_cols;     // [P+1]
+  std::vector<int> S, S_unpruned;       // [Mtot]
+  std::vector<int> meas_prob_h;         // [Mtot]
+  std::vector<long long> col_off;       // [Mtot+1] kept columns
+  std::vector<long long> unpruned_off;  // [Mtot+1] unpruned entries
+  std::vector<long long> keep;          // [T] unpruned index of each column
+  std::vector<double> a;                // [Mtot]
+  std::vector<double> rho, gamma, Qa;   // [P]
+  std::vector<double> bundle_cum;       // [nb]
+  std::vector<std::pair<long long, long long>> index_sets;  // column ranges
+  std::vector<double> xi_h;             // [P][R][dim]
+  std::vector<double> zeta_kept;        // [T][dim] (when available)
+
+  // device buffers (all in `allocs`)
+  std::vector<void*> allocs;
+  float* theta = nullptr;
+  void* cost = nullptr;
+  float* q = nullptr;
+  double* q64 = nullptr;
+  float* lam = nullptr;
+  double* pm = nullptr;
+  double* delta = nullptr;
+  double* phat = nullptr;
+  double* p = nullptr;
+  double* t = nullptr;
+  double* blk = nullptr;
+  unsigned* counter = nullptr;
+  double* stat = nullptr;
+  float* diag_wc = nullptr;
+  float* diag_lb = nullptr;
+  float* diag_res = nullptr;
+  double* diag_out = nullptr;
+  unsigned long long* passes = nullptr;
+  int* err_d = nullptr;
+  int* meas_prob = nullptr;
+  float* rho_m = nullptr;
+  float* irho_m = nullptr;
+  double* a_d = nullptr;
+  double* alpha_d = nullptr;
+  int* S_d = nullptr;
+  int* prob_meas_d = nullptr;
+  double* rho_d = nullptr;
+  double* gamma_d = nullptr;
+  long long* col_off_d = nullptr;
+  long long* prob_cols_d = nullptr;
+  int* col_meas = nullptr;
+  double* bundle_cum_d = nullptr;
+  long long* iter_d = nullptr;
+  int* bundle_cur = nullptr;
+  int* bundle_prev = nullptr;
+  float* partials = nullptr;
+  int max_slots = 0;
+
+  // schedules and launch configuration
+  std::vector<void*> sched_allocs;
+  mam::Sched* sched_d = nullptr;
+  mam_kernel_config cfg{};
+  int grid = 0;
+  size_t smem = 0;
+  cudaGraphExec_t graph = nullptr;
+
+  // host mirrors
+  long long iter = 0;
+  long long diag_iter = -1;
+
+  // per-kernel timing (mam_profile_enable)
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;
+  size_t prof_used = 0;
+
+  mam::BackwardState* bwd = nullptr;
+};
+
+namespace mam {
+
+mam_status fail(mam_problem* h, mam_status code, const std::string& msg);
+mam_status cuda_fail(mam_problem* h, cudaError_t e, const char* where);
+
+// Device allocation recorded in the handle (freed by mam_destroy).
+template <typename T>
+mam_status dalloc(mam_problem* h, T** ptr, size_t count, const char* what) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MAM_ERR_OOM,
+                std::string("cudaMalloc failed for ") + what + " (" +
+                    std::to_string(count * sizeof(T)) + " bytes)");
+  }
+  h->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return MAM_OK;
+}
+size_t cost_elem_size(int dt);
+mam_status apply_config(mam_problem* h, const mam_kernel_config& c);
+mam_status check_config(const mam_problem* h, const mam_kernel_config& c);
+mam_kernel_config default_config(const mam_problem* h);
+mam_status run_iterations(mam_problem* h, int n, bool diag_last);
+mam_status launch_iteration(mam_problem* h, bool diag);
+mam_status sync(mam_problem* h);
+ColArgs col_args(const mam_problem* h);
+AvgArgs avg_args(const mam_problem* h, int reduce, int diag);
+int avg_blocks(const mam_problem* h);
+size_t column_smem_bytes(const mam_problem* h, int stages);
+void free_backward(mam_problem* h);
+mam_status reset_state(mam_problem* h);
+
+}  // namespace mam

@@ -1,0 +1,219 @@
+"""Python binding of libmam with the C ABI's names (argument marshalling only).
+
+``Mam`` wraps one problem handle (or a batch of problems).  Every method is a
+direct call of the C function of the same name in include/mam.h; numpy arrays
+are passed as host pointers and, where the ABI accepts device pointers, torch
+CUDA tensors as device pointers.  Nothing here computes any part of the
+method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _capi
+from ._capi import MamDesc, MamKernelConfig, MamObjective, check
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _DescKeep:
+    """Owns the contiguous arrays a mam_desc points into."""
+
+    def __init__(self, problem, cost_dtype, theta0_mode, diag_mode, n_bundles,
+                 seed, rho, gamma, stream):
+        M = len(problem.q)
+        xi = np.ascontiguousarray(problem.xi, dtype=np.float64)
+        if xi.ndim == 1:
+            xi = xi[:, None]
+        R, dim = xi.shape
+        self.S = np.ascontiguousarray([len(q) for q in problem.q], dtype=np.int32)
+        self.q = np.ascontiguousarray(np.concatenate(problem.q), dtype=np.float64)
+        self.alpha = np.ascontiguousarray(problem.alpha, dtype=np.float64)
+        self.xi = xi
+        self.zeta = None
+        if problem.zeta is not None:
+            z = [np.asarray(v, dtype=np.float64).reshape(len(problem.q[m]), dim)
+                 for m, v in enumerate(problem.zeta)]
+            self.zeta = np.ascontiguousarray(np.concatenate(z))
+        self.cost = None
+        if getattr(problem, "cost", None) is not None:
+            self.cost = np.ascontiguousarray(np.concatenate(
+                [np.asarray(c, dtype=np.float64).reshape(len(problem.q[m]), R)
+                 for m, c in enumerate(problem.cost)]))
+        d = MamDesc()
+        d.M, d.R, d.dim = M, R, dim
+        d.S = self.S.ctypes.data_as(C.POINTER(C.c_int32))
+        d.zeta = _dptr(self.zeta) if self.zeta is not None else None
+        d.q = _dptr(self.q)
+        d.alpha = _dptr(self.alpha)
+        d.xi = _dptr(self.xi)
+        d.cost = _dptr(self.cost) if self.cost is not None else None
+        d.rho = float(problem.rho if rho is None else rho)
+        g = getattr(problem, "gamma", math.inf) if gamma is None else gamma
+        d.gamma = float(g)
+        nb = getattr(problem, "n_bundles", 1) if n_bundles is None else n_bundles
+        d.n_bundles = int(nb)
+        d.seed = int(seed)
+        d.cost_dtype = _capi.COST_DTYPES[cost_dtype]
+        d.theta0_mode = {"spread": 0, "zero": 1}[theta0_mode]
+        d.diag_mode = _capi.DIAG_MODES[diag_mode]
+        d.stream = stream
+        self.desc = d
+
+
+class Mam:
+    """One MAM problem (or a batch) living on the GPU."""
+
+    def __init__(self, problem=None, *, problems: Optional[Sequence] = None,
+                 cost_dtype: str = "f32", theta0: str = "spread",
+                 diag: str = "last", n_bundles: Optional[int] = None,
+                 seed: int = 0, rho: Optional[float] = None,
+                 gamma: Optional[float] = None, stream=None):
+        L = _capi.lib()
+        if (problem is None) == (problems is None):
+            raise ValueError("give exactly one of problem / problems")
+        probs = [problem] if problems is None else list(problems)
+        st = None
+        if stream is not None:
+            st = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        keeps = [_DescKeep(p, cost_dtype, theta0, diag, n_bundles, seed, rho, gamma, st)
+                 for p in probs]
+        self._h = C.c_void_p()
+        if problems is None:
+            check(L.mam_create(C.byref(keeps[0].desc), C.byref(self._h)))
+        else:
+            arr = (MamDesc * len(keeps))(*[k.desc for k in keeps])
+            check(L.mam_batch_create(len(keeps), arr, C.byref(self._h)))
+        self.batched = problems is not None
+        P, Mt, R, T, ld = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+        check(L.mam_get_sizes(self._h, C.byref(P), C.byref(Mt), C.byref(R), C.byref(T),
+                              C.byref(ld)), self._h)
+        self.n_problems, self.n_measures = P.value, Mt.value
+        self.R, self.T, self.ld = R.value, T.value, ld.value
+        self.dim = keeps[0].xi.shape[1]
+        self.S_unpruned = np.concatenate([k.S for k in keeps])
+        self.n_unpruned = int(self.S_unpruned.sum())
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _capi.lib().mam_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, status):
+        check(status, self._h)
+
+    # -- iteration
+    def step(self, n_iters: int = 1):
+        self._check(_capi.lib().mam_step(self._h, int(n_iters)))
+
+    def solve(self, max_iters: int, gap_tol: float = 1e-4, w_ref: float = 0.0,
+              check_every: int = 10):
+        it, gap = C.c_int32(), C.c_double()
+        self._check(_capi.lib().mam_solve(self._h, int(max_iters), float(gap_tol),
+                                          float(w_ref), int(check_every),
+                                          C.byref(it), C.byref(gap)))
+        return it.value, gap.value
+
+    def objective(self, index: int = 0) -> dict:
+        o = MamObjective()
+        self._check(_capi.lib().mam_objective(self._h, int(index), C.byref(o)))
+        return o.as_dict()
+
+    # -- outputs
+    def barycenter(self) -> np.ndarray:
+        out = np.empty((self.n_problems, self.R), dtype=np.float64)
+        self._check(_capi.lib().mam_get_barycenter(self._h, out.ctypes.data, 0))
+        return out if self.batched else out[0]
+
+    def barycenter_into(self, tensor):
+        """Copy p into a CUDA float64 tensor of n_problems*R elements."""
+        assert tensor.is_cuda and tensor.dtype.is_floating_point and tensor.element_size() == 8
+        assert tensor.is_contiguous() and tensor.numel() == self.n_problems * self.R
+        self._check(_capi.lib().mam_get_barycenter(self._h, C.c_void_p(tensor.data_ptr()), 1))
+        return tensor
+
+    def marginals(self) -> np.ndarray:
+        out = np.empty((self.n_measures, self.R), dtype=np.float64)
+        self._check(_capi.lib().mam_get_marginals(self._h, out.ctypes.data, 0))
+        return out
+
+    def theta(self) -> np.ndarray:
+        out = np.empty((self.T, self.R), dtype=np.float32)
+        self._check(_capi.lib().mam_get_theta(self._h, out.ctypes.data))
+        return out
+
+    def pruned_sizes(self) -> np.ndarray:
+        out = np.empty(self.n_measures, dtype=np.int32)
+        self._check(_capi.lib().mam_get_pruned_sizes(self._h, out.ctypes.data))
+        return out
+
+    # -- checkpoints
+    def get_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(_capi.lib().mam_get_state(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(_capi.lib().mam_get_state(self._h, buf, C.byref(n)))
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(_capi.lib().mam_set_state(self._h, buf, len(blob)))
+
+    # -- configuration
+    def config(self) -> dict:
+        c = MamKernelConfig()
+        self._check(_capi.lib().mam_get_config(self._h, C.byref(c)))
+        return c.as_dict()
+
+    def set_config(self, **kw):
+        c = MamKernelConfig()
+        self._check(_capi.lib().mam_get_config(self._h, C.byref(c)))
+        for k, v in kw.items():
+            setattr(c, k, int(v))
+        self._check(_capi.lib().mam_set_config(self._h, C.byref(c)))
+
+    def autotune(self, iters: int = 5) -> dict:
+        c = MamKernelConfig()
+        self._check(_capi.lib().mam_autotune(self._h, int(iters), C.byref(c)))
+        return c.as_dict()
+
+    # -- measurement
+    def profile_enable(self, enable: bool = True):
+        self._check(_capi.lib().mam_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        c, a, n = C.c_double(), C.c_double(), C.c_int64()
+        self._check(_capi.lib().mam_profile_read(self._h, C.byref(c), C.byref(a), C.byref(n)))
+        return {"column_ms": c.value, "average_ms": a.value, "iterations": n.value}
+
+    # -- differentiation
+    def forward_record(self, K: int, ckpt_every: int = 20):
+        self._check(_capi.lib().mam_forward_record(self._h, int(K), int(ckpt_every)))
+
+    def backward(self, grad_p, want=("q", "zeta", "xi")):
+        g = np.ascontiguousarray(grad_p, dtype=np.float64).reshape(self.R)
+        gq = np.zeros(self.n_unpruned) if "q" in want else None
+        gz = np.zeros((self.n_unpruned, self.dim)) if "zeta" in want else None
+        gx = np.zeros((self.R, self.dim)) if "xi" in want else None
+        ptr = lambda a: a.ctypes.data if a is not None else None
+        self._check(_capi.lib().mam_backward(self._h, g.ctypes.data, ptr(gq), ptr(gz), ptr(gx)))
+        return gq, gz, gx

@@ -1,0 +1,105 @@
+"""The C ABI library builds, loads and exports every symbol include/mam.h
+declares; argument validation happens before any device call, so the
+invalid-argument paths are checked here without a GPU."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2309_05315_gb300 import _capi
+from paper_2309_05315_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return _capi.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mam.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mam_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    # and the Python binding declares every one of them
+    assert set(names) <= set(_capi.exported_names())
+
+
+def make_desc(M=2, R=4, S=(3, 3), q=None, gamma=math.inf, rho=1.0, **kw):
+    S = np.asarray(S, dtype=np.int32)
+    n = int(S.sum())
+    q = np.full(n, 1.0 / S[0]) if q is None else np.asarray(q, dtype=np.float64)
+    keep = dict(S=S, q=q, zeta=np.zeros((n, 2)), alpha=np.full(M, 1.0 / M),
+                xi=np.zeros((R, 2)))
+    d = _capi.MamDesc()
+    d.M, d.R, d.dim = M, R, 2
+    d.S = keep["S"].ctypes.data_as(C.POINTER(C.c_int32))
+    for k in ("q", "zeta", "alpha", "xi"):
+        setattr(d, k, keep[k].ctypes.data_as(C.POINTER(C.c_double)))
+    d.cost = None
+    d.rho, d.gamma = rho, gamma
+    d.n_bundles, d.seed, d.cost_dtype, d.theta0_mode, d.diag_mode = 0, 0, 0, 0, 0
+    d.stream = None
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, keep
+
+
+@pytest.mark.parametrize("case", [
+    dict(M=0),
+    dict(R=0),
+    dict(R=20000),
+    dict(dim=4),
+    dict(rho=0.0),
+    dict(rho=-1.0),
+    dict(gamma=-0.5),
+    dict(cost_dtype=7),
+    dict(theta0_mode=3),
+    dict(n_bundles=5),
+])
+def test_invalid_descriptor_fields(L, case):
+    d, keep = make_desc()
+    for k, v in case.items():
+        setattr(d, k, v)
+    h = C.c_void_p()
+    st = L.mam_create(C.byref(d), C.byref(h))
+    assert st == 1 and not h.value
+    assert len(L.mam_last_error(None)) > 0
+
+
+@pytest.mark.parametrize("q", [
+    [0.5, 0.5, 0.0, 0.4, 0.6, float("nan")],   # NaN weight
+    [0.5, 0.5, 0.0, -0.1, 0.6, 0.5],           # negative weight
+    [0.0, 0.0, 0.0, 0.4, 0.6, 0.0],            # measure without mass
+    [0.5, 0.5, 0.0, 0.4, 0.7, 0.0],            # unequal masses, balanced
+])
+def test_invalid_weights(L, q):
+    d, keep = make_desc(q=q)
+    h = C.c_void_p()
+    assert L.mam_create(C.byref(d), C.byref(h)) == 1
+    assert not h.value
+
+
+def test_null_arguments(L):
+    assert L.mam_step(None, 1) == 1
+    assert L.mam_objective(None, 0, None) == 1
+    assert L.mam_create(None, None) == 1
+    L.mam_destroy(None)  # allowed
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(_capi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_capi, "_lib", None)
+    with pytest.raises(ImportError):
+        _capi.lib()

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (the ones the method's use fixes):
+* iterates, first 50 iterations: ||theta_gpu - theta_ref||_1 / sum_m Q_m and
+  ||p_gpu - p_ref||_1 / sum_m a_m Q_m below 1e-5;
+* objective after the full run: |W_gpu - W_ref| / |W_ref| below 1e-4.
+The DR map is nonexpansive, so FP32 rounding adds up across iterations
+instead of growing geometrically; that is what makes an iterate tolerance
+meaningful.
+"""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+from oracle.mam_oracle import MamOracle, prepare, project_simplex
+from workloads import Problem, config1, config2, grid_points, problem_from_images, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+ITER_TOL = 1e-5
+OBJ_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def Mam():
+    from paper_2309_05315_gb300.build import build
+    build()
+    from paper_2309_05315_gb300 import Mam as _Mam
+    return _Mam
+
+
+def masses(prep):
+    Q = sum(float(q.sum()) for q in prep.q)
+    Qa = sum(prep.a[m] * float(prep.q[m].sum()) for m in range(prep.M))
+    return Q, Qa
+
+
+def flat(th):
+    return np.concatenate([t.ravel() for t in th])
+
+
+def compare_trajectory(Mam, prob, iters, cost_dtype="f32", oracle_cost="f64",
+                       n_bundles=1, seed=0, gamma=None, theta0="spread",
+                       config=None, tol=ITER_TOL):
+    g = math.inf if gamma is None else gamma
+    prep = prepare(prob, oracle_cost)
+    orc = MamOracle(prep, prob.rho, gamma=g, n_bundles=n_bundles, seed=seed,
+                    theta0=theta0)
+    Q, Qa = masses(prep)
+    worst = 0.0
+    with Mam(prob, cost_dtype=cost_dtype, diag="never", n_bundles=n_bundles,
+             seed=seed, gamma=g, theta0=theta0) as gpu:
+        if config:
+            gpu.set_config(**config)
+        assert gpu.T == sum(int(s) for s in prep.S)
+        np.testing.assert_array_equal(gpu.pruned_sizes(), prep.S)
+        for k in range(iters):
+            orc.step(diagnostics=False)
+            gpu.step(1)
+            th = gpu.theta().astype(np.float64)
+            e_th = np.abs(th.ravel() - flat(orc.theta)).sum() / Q
+            e_p = np.abs(gpu.barycenter() - orc.barycenter()).sum() / Qa
+            worst = max(worst, e_th, e_p)
+            assert e_th <= tol, (k, e_th)
+            assert e_p <= tol, (k, e_p)
+    return worst
+
+
+def test_config1_first_50_iterations(Mam):
+    compare_trajectory(Mam, config1(), 50)
+
+
+def test_config1_objective_after_500(Mam):
+    prob = config1()
+    prep = prepare(prob)
+    orc = MamOracle(prep, prob.rho)
+    orc.run(499)
+    ref = orc.step(diagnostics=True)
+    with Mam(prob, cost_dtype="f32", diag="last") as gpu:
+        gpu.step(500)
+        o = gpu.objective()
+    assert o["iter"] == 500
+    assert abs(o["w_hat"] - ref["w_hat"]) <= OBJ_TOL * abs(ref["w_hat"])
+    assert abs(o["lower_bound"] - ref["lower_bound"]) <= OBJ_TOL * abs(ref["lower_bound"])
+    assert abs(o["dist_pihat"] - ref["dist_pihat"]) <= 1e-3 * ref["dist_pihat"] + 1e-9
+    assert abs(o["fp_resid"] - ref["fp_resid"]) <= 1e-2 * ref["fp_resid"] + 1e-9
+    assert abs(o["dp_norm"] - ref["dp_norm"]) <= 1e-2 * ref["dp_norm"] + 1e-9
+    assert o["t"] == 1.0
+
+
+@pytest.mark.parametrize("R_side,M", [(3, 3), (5, 2), (7, 4), (11, 3)])
+def test_ragged_rows(Mam, R_side, M):
+    """R = 9, 25, 49, 121: columns not a multiple of the float4/8-element
+    padding, tiny supports, several CTAs per measure."""
+    prob = tiny_problem(100 + R_side, M=M, K=R_side, rho=5.0, density=0.6)
+    compare_trajectory(Mam, prob, 30)
+
+
+def test_ragged_R_not_grid(Mam):
+    """R = 37 points and 1-point and 2-point measures (S_m after pruning)."""
+    rng = np.random.default_rng(5)
+    xi = rng.uniform(size=(37, 2))
+    zeta = [rng.uniform(size=(4, 2)) for _ in range(3)]
+    q = [np.array([0.0, 1.0, 0.0, 0.0]), np.array([0.5, 0.0, 0.5, 0.0]),
+         np.array([0.25, 0.25, 0.25, 0.25])]
+    prob = Problem("ragged", xi=xi, zeta=zeta, q=q, alpha=np.full(3, 1 / 3), rho=10.0)
+    compare_trajectory(Mam, prob, 40)
+
+
+def test_single_row_and_single_measure(Mam):
+    xi = np.array([[0.3, 0.3]])
+    prob = Problem("R1", xi=xi, zeta=[np.random.default_rng(0).uniform(size=(5, 2))],
+                   q=[np.full(5, 0.2)], alpha=np.array([1.0]), rho=3.0)
+    compare_trajectory(Mam, prob, 10)
+
+
+def test_dimension_one_and_three(Mam):
+    rng = np.random.default_rng(9)
+    for dim in (1, 3):
+        xi = rng.uniform(size=(40, dim))
+        zeta = [rng.uniform(size=(9, dim)) for _ in range(2)]
+        q = [rng.uniform(0.1, 1, size=9) for _ in range(2)]
+        q = [v / v.sum() for v in q]
+        prob = Problem(f"dim{dim}", xi=xi, zeta=zeta, q=q, alpha=np.array([0.4, 0.6]),
+                       rho=20.0)
+        compare_trajectory(Mam, prob, 25)
+
+
+def test_general_cost_matrix(Mam):
+    rng = np.random.default_rng(4)
+    prob = tiny_problem(7, M=3, K=5, rho=4.0, density=0.7)
+    prob.cost = [np.abs(rng.normal(size=(len(q), prob.R))) for q in prob.q]
+    compare_trajectory(Mam, prob, 30)
+
+
+def test_theta0_zero(Mam):
+    compare_trajectory(Mam, tiny_problem(8, M=3, K=6, rho=10.0), 30, theta0="zero")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_reduced_precision_costs(Mam, dtype):
+    """The oracle rounds its costs the same way (FP64 -> FP32 -> dtype)."""
+    compare_trajectory(Mam, config1(), 50, cost_dtype=dtype, oracle_cost=dtype)
+
+
+@pytest.mark.parametrize("gamma", [0.003, 0.05])
+def test_unbalanced(Mam, gamma):
+    prob = tiny_problem(9, M=4, K=8, rho=20.0, masses=[0.6, 1.0, 1.5, 2.0])
+    prob.gamma = gamma
+    compare_trajectory(Mam, prob, 40, gamma=gamma)
+
+
+def test_randomized_bundles(Mam):
+    prob = tiny_problem(10, M=6, K=7, rho=15.0, masses=[0.5, 1, 1.5, 0.8, 1.2, 2.0])
+    compare_trajectory(Mam, prob, 40, n_bundles=3, seed=1234, gamma=0.02)
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(threads=32, vec=2, stages=2),
+    dict(threads=64, vec=1, stages=3),
+    dict(threads=32, vec=1, stages=4, ctas_per_sm=1),
+    dict(threads=96, vec=1, stages=2, ctas_per_sm=2),
+])
+def test_kernel_configurations(Mam, cfg):
+    compare_trajectory(Mam, config1(), 20, config=cfg)
+
+
+def test_cold_start_bisection_depths(Mam):
+    for depth in (0, 12, 30):
+        compare_trajectory(Mam, config1(), 5, config=dict(bisect_depth=depth))
+
+
+def test_diagnostics_match_oracle(Mam):
+    prob = tiny_problem(11, M=3, K=6, rho=8.0, masses=[0.7, 1.0, 1.3])
+    prob.gamma = 0.01
+    prep = prepare(prob)
+    orc = MamOracle(prep, prob.rho, gamma=0.01)
+    orc.run(29)
+    ref = orc.step(diagnostics=True)
+    with Mam(prob, diag="last", gamma=0.01) as gpu:
+        gpu.step(30)
+        o = gpu.objective()
+    for k in ("w_hat", "lower_bound", "f_unbal"):
+        assert abs(o[k] - ref[k]) <= 1e-4 * abs(ref[k]), k
+    assert abs(o["dist_pihat"] - ref["dist_pihat"]) <= 1e-3 * ref["dist_pihat"]
+    assert abs(o["t"] - ref["t"]) <= 1e-4
+
+
+def test_bitwise_determinism_and_resume(Mam):
+    prob = config1()
+    with Mam(prob, diag="never") as a, Mam(prob, diag="never") as b:
+        a.step(37)
+        b.step(20)
+        blob = b.get_state()
+        b.step(5)          # diverge, then come back
+        b.set_state(blob)
+        b.step(17)
+        assert np.array_equal(a.theta(), b.theta())
+        assert np.array_equal(a.barycenter(), b.barycenter())
+
+
+def test_graph_replay_equals_single_launches(Mam):
+    prob = config1()
+    with Mam(prob, diag="never") as a, Mam(prob, diag="never") as b:
+        a.step(23)               # two captured 10-iteration graphs + 3 launches
+        for _ in range(23):
+            b.step(1)
+        assert np.array_equal(a.theta(), b.theta())
+
+
+def test_batched_matches_separate_problems(Mam):
+    probs = [tiny_problem(200 + i, M=2 + i % 3, K=6, rho=6.0) for i in range(5)]
+    with Mam(problems=probs, diag="last") as batch:
+        batch.step(30)
+        pb = batch.barycenter()
+        objs = [batch.objective(i) for i in range(len(probs))]
+    for i, prob in enumerate(probs):
+        prep = prepare(prob)
+        orc = MamOracle(prep, prob.rho)
+        orc.run(29)
+        ref = orc.step(diagnostics=True)
+        Q, Qa = masses(prep)
+        assert np.abs(pb[i] - orc.barycenter()).sum() / Qa <= ITER_TOL
+        assert abs(objs[i]["w_hat"] - ref["w_hat"]) <= 1e-4 * ref["w_hat"]
+
+
+def test_solve_reaches_gap(Mam):
+    prob = tiny_problem(12, M=3, K=4, rho=5.0)
+    with Mam(prob) as gpu:
+        it, gap = gpu.solve(20000, gap_tol=1e-4, check_every=50)
+        o = gpu.objective()
+    assert gap <= 1e-4 and it < 20000
+    assert abs(o["w_hat"] - o["lower_bound"]) <= 1e-4 * abs(o["lower_bound"])
+
+
+def test_config2_full_size_iterates(Mam):
+    """The bench workload (60x60 nested ellipses, R=3600) in the bench's
+    launch configuration: full iterates against the oracle for 5 steps."""
+    prob = config2()
+    compare_trajectory(Mam, prob, 5)
+
+
+def test_config2_sampled_columns_after_warm_steps(Mam):
+    """After 60 iterations, one more GPU step is checked column by column
+    against an FP64 projection of the same input state."""
+    prob = config2()
+    prep = prepare(prob, "f32")
+    with Mam(prob, diag="never") as gpu:
+        gpu.step(60)
+        th0 = gpu.theta().astype(np.float64)
+        pm = gpu.marginals()
+        p = gpu.barycenter()
+        t = gpu.objective()["t_next"]
+        gpu.step(1)
+        th1 = gpu.theta().astype(np.float64)
+    rng = np.random.default_rng(0)
+    offs = np.concatenate([[0], np.cumsum(prep.S)])
+    for col in rng.choice(int(offs[-1]), size=200, replace=False):
+        m = int(np.searchsorted(offs, col, side="right") - 1)
+        s = col - offs[m]
+        d = t * (p - pm[m]) / prep.S[m]
+        w = th0[col] + 2 * d - prep.c[m][s] / prob.rho
+        x, _ = project_simplex(w, prep.q[m][s])
+        ref = x[0] - d
+        assert np.abs(th1[col] - ref).sum() <= 1e-5 * prep.q[m][s] + 1e-9, col
+
+
+def test_maximum_R(Mam):
+    """R = 12288 (the largest column a CTA holds) on a tiny problem."""
+    K1, K2 = 96, 128
+    i, j = np.meshgrid(np.arange(K1), np.arange(K2), indexing="ij")
+    xi = np.stack([i.ravel() / (K1 - 1), j.ravel() / (K2 - 1)], 1)
+    rng = np.random.default_rng(3)
+    zeta = [rng.uniform(size=(6, 2)) for _ in range(2)]
+    q = [np.full(6, 1 / 6), np.full(6, 1 / 6)]
+    prob = Problem("maxR", xi=xi, zeta=zeta, q=q, alpha=np.array([0.5, 0.5]), rho=50.0)
+    compare_trajectory(Mam, prob, 6)
