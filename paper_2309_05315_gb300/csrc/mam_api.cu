@@ -150,39 +150,6 @@ namespace mam {
 
 // ----------------------------------------------------------- schedules
 
-static void build_sched_host(const mam_problem* h, long long c0, long long c1,
-                             int G, SchedHost& out) {
-  const long long n = c1 - c0;
-  out.col_begin = c0;
-  out.col_end = c1;
-  out.cta_seg_begin.assign(G + 1, 0);
-  out.segs.clear();
-  out.slot_begin.assign(h->Mtot, 0);
-  out.slot_end.assign(h->Mtot, 0);
-  std::vector<char> seen(h->Mtot, 0);
-  int nseg = 0;
-  int m = int(std::upper_bound(h->col_off.begin(), h->col_off.end(), c0) -
-              h->col_off.begin()) - 1;
-  for (int b = 0; b < G; ++b) {
-    out.cta_seg_begin[b] = nseg;
-    const long long cb = c0 + n * b / G, ce = c0 + n * (b + 1) / G;
-    long long c = cb;
-    while (c < ce) {
-      while (h->col_off[m + 1] <= c) ++m;
-      const long long e = std::min(ce, h->col_off[m + 1]);
-      out.segs.push_back(make_int4(m, int(c), int(e), nseg));
-      if (!seen[m]) {
-        seen[m] = 1;
-        out.slot_begin[m] = nseg;
-      }
-      out.slot_end[m] = nseg + 1;
-      ++nseg;
-      c = e;
-    }
-  }
-  out.cta_seg_begin[G] = nseg;
-}
-
 static void free_sched(mam_problem* h) {
   for (void* p : h->sched_allocs) cudaFree(p);
   h->sched_allocs.clear();
@@ -206,7 +173,8 @@ static mam_status sched_alloc(mam_problem* h, void** p, size_t bytes) {
 
 size_t column_smem_bytes(const mam_problem* h, int stages) {
   return size_t(stages) * h->ld * (sizeof(float) + cost_elem_size(h->cost_dtype)) +
-         4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4);
+         4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4) +
+         kRedSlots * sizeof(double);
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
@@ -243,7 +211,9 @@ mam_kernel_config default_config(const mam_problem* h) {
     const int nt = std::max(32, round_up((ld4 + nv - 1) / nv, 32));
     if (nt > column_max_threads(nv)) continue;
     const double util = double(ld4) / (double(nt) * nv);
-    const double score = util - 0.004 * std::abs(nv - 4);
+    // Prefer covering the column with few warps: every threshold-search pass
+    // ends in a CTA-wide reduction whose latency grows with the warp count.
+    const double score = util - 0.01 * (nt / 32);
     if (score > best_score + 1e-12) {
       best_score = score;
       best.threads = nt;
@@ -277,44 +247,17 @@ mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
   G = std::max(1LL, std::min(G, max_cols));
 
   free_sched(h);
-  std::vector<SchedHost> hs(h->index_sets.size());
-  int max_slots = 0;
-  for (size_t i = 0; i < hs.size(); ++i) {
-    build_sched_host(h, h->index_sets[i].first, h->index_sets[i].second, int(G), hs[i]);
-    max_slots = std::max(max_slots, int(hs[i].segs.size()));
-  }
-  std::vector<Sched> sd(hs.size());
-  for (size_t i = 0; i < hs.size(); ++i) {
-    void *a, *b, *c2, *d;
-    MAM_TRY(sched_alloc(h, &a, hs[i].cta_seg_begin.size() * sizeof(int)));
-    MAM_TRY(sched_alloc(h, &b, hs[i].segs.size() * sizeof(int4)));
-    MAM_TRY(sched_alloc(h, &c2, h->Mtot * sizeof(int)));
-    MAM_TRY(sched_alloc(h, &d, h->Mtot * sizeof(int)));
-    MAM_CUDA(cudaMemcpyAsync(a, hs[i].cta_seg_begin.data(), hs[i].cta_seg_begin.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream), "sched upload");
-    if (!hs[i].segs.empty())
-      MAM_CUDA(cudaMemcpyAsync(b, hs[i].segs.data(), hs[i].segs.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream), "sched upload");
-    MAM_CUDA(cudaMemcpyAsync(c2, hs[i].slot_begin.data(), h->Mtot * sizeof(int), cudaMemcpyHostToDevice, h->stream), "sched upload");
-    MAM_CUDA(cudaMemcpyAsync(d, hs[i].slot_end.data(), h->Mtot * sizeof(int), cudaMemcpyHostToDevice, h->stream), "sched upload");
-    sd[i].cta_seg_begin = static_cast<int*>(a);
-    sd[i].segs = static_cast<int4*>(b);
-    sd[i].slot_begin = static_cast<int*>(c2);
-    sd[i].slot_end = static_cast<int*>(d);
-    sd[i].col_begin = hs[i].col_begin;
-    sd[i].col_end = hs[i].col_end;
+  std::vector<Sched> sd(h->index_sets.size());
+  for (size_t i = 0; i < sd.size(); ++i) {
+    sd[i].col_begin = h->index_sets[i].first;
+    sd[i].col_end = h->index_sets[i].second;
+    sd[i].meas_begin = h->index_meas[i].first;
+    sd[i].meas_end = h->index_meas[i].second;
   }
   void* sp;
   MAM_TRY(sched_alloc(h, &sp, sd.size() * sizeof(Sched)));
   MAM_CUDA(cudaMemcpyAsync(sp, sd.data(), sd.size() * sizeof(Sched), cudaMemcpyHostToDevice, h->stream), "sched upload");
   h->sched_d = static_cast<Sched*>(sp);
-  if (max_slots > h->max_slots) {
-    if (h->partials) {
-      cudaFree(h->partials);
-      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void*)h->partials));
-      h->partials = nullptr;
-    }
-    MAM_TRY(dalloc(h, &h->partials, size_t(max_slots) * h->ld, "partial row sums"));
-    h->max_slots = max_slots;
-  }
   h->cfg = c;
   h->grid = int(G);
   h->smem = smem;
@@ -324,20 +267,37 @@ mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
 
 // ------------------------------------------------------------ iteration
 
+Draw draw_args(const mam_problem* h) {
+  Draw d;
+  d.nb = h->nb;
+  d.cum = h->bundle_cum_d;
+  d.seed = h->seed;
+  return d;
+}
+
 ColArgs col_args(const mam_problem* h) {
   ColArgs a{};
   a.theta = h->theta;
   a.cost = h->cost;
   a.q = h->q;
   a.lam = h->lam;
+  a.nact = h->nact;
+  a.col_meas = h->col_meas;
   a.delta = h->delta;
-  a.t = h->t;
+  a.blk = h->blk;
+  a.nblk = avg_blocks(h);
+  a.rho_p = h->rho_d;
+  a.gamma_p = h->gamma_d;
+  a.t_used = h->t_used;
   a.meas_prob = h->meas_prob;
   a.rho = h->rho_m;
   a.inv_rho = h->irho_m;
-  a.partials = h->partials;
+  a.acc = h->acc;
+  a.fx_scale = float(h->fx_scale);
   a.sched = h->sched_d;
-  a.bundle_cur = h->nb > 1 ? h->bundle_cur : nullptr;
+  a.draw = draw_args(h);
+  a.iter = h->iter_d;
+  a.done = h->done;
   a.diag_wc = h->diag_wc;
   a.diag_lb = h->diag_lb;
   a.diag_res = h->diag_res;
@@ -354,35 +314,27 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   AvgArgs a{};
   a.P = h->P;
   a.R = h->R;
-  a.ld = h->ld;
   a.prob_meas = h->prob_meas_d;
-  a.S = h->S_d;
+  a.Sd = h->Sd_d;
+  a.inv_S = h->invS_d;
   a.a = h->a_d;
-  a.rho = h->rho_d;
-  a.gamma = h->gamma_d;
-  a.partials = h->partials;
+  a.acc = h->acc;
+  a.fx_inv_scale = 1.0 / h->fx_scale;
   a.sched = h->sched_d;
-  a.bundle_cur = h->nb > 1 ? h->bundle_cur : nullptr;
-  a.bundle_prev = h->nb > 1 ? h->bundle_prev : nullptr;
+  a.draw = draw_args(h);
+  a.iter = h->iter_d;
+  a.t_used = h->t_used;
   a.reduce = reduce;
   a.diag = diag;
   a.pm = h->pm;
   a.p = h->p;
   a.delta = h->delta;
   a.phat = h->phat;
-  a.t = h->t;
   a.blk = h->blk;
-  a.counter = h->counter;
-  a.stat = h->stat;
-  a.nb = h->nb;
-  a.bundle_cum = h->bundle_cum_d;
-  a.seed = h->seed;
-  a.iter = h->iter_d;
-  a.bundle_next = h->bundle_cur;
   return a;
 }
 
-int avg_blocks(const mam_problem* h) { return (h->R + 255) / 256; }
+int avg_blocks(const mam_problem* h) { return (h->R + kAvgRows - 1) / kAvgRows; }
 
 static mam_status prof_event(mam_problem* h, cudaEvent_t* ev) {
   if (h->prof_used >= h->prof_events.size()) {
@@ -400,17 +352,18 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
     for (auto& e : ev) MAM_TRY(prof_event(h, &e));
     MAM_CUDA(cudaEventRecord(ev[0], h->stream), "cudaEventRecord");
   }
-  if (diag && h->nb > 1) {
-    // Lower bound of every measure for the same v^k the column step uses.
-    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta, h->t, h->meas_prob,
-                       h->rho_m, h->col_meas, h->T, h->R, h->ld, h->diag_lb,
-                       h->stream),
-             "lower-bound kernel");
-  }
   const ColArgs ca = col_args(h);
   MAM_CUDA(launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
                          h->smem, h->stream, ca),
            "column kernel launch");
+  if (diag && h->nb > 1) {
+    // Lower bound of every measure for the v^k the column step just used
+    // (the fused value covers only the drawn bundle).
+    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta, h->t_used, h->meas_prob,
+                       h->rho_m, h->col_meas, h->T, h->R, h->ld, h->diag_lb,
+                       h->stream),
+             "lower-bound kernel");
+  }
   if (h->profiling) MAM_CUDA(cudaEventRecord(ev[1], h->stream), "cudaEventRecord");
   const AvgArgs aa = avg_args(h, 1, diag ? 1 : 0);
   MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
@@ -479,23 +432,24 @@ mam_status sync(mam_problem* h) {
 // ------------------------------------------------------------ creation
 
 mam_status reset_state(mam_problem* h) {
-  MAM_CUDA(launch_init_theta(h->theta, h->lam, h->q64, h->T, h->R, h->ld,
+  MAM_CUDA(launch_init_theta(h->theta, h->lam, h->nact, h->q64, h->T, h->R, h->ld,
                              h->theta0_mode, h->stream),
            "init kernel");
   MAM_CUDA(launch_rowsum(h->theta, h->col_off_d, h->Mtot, h->R, h->ld, h->pm,
                          h->stream),
            "rowsum kernel");
+  const size_t MR = size_t(h->Mtot) * h->R;
   MAM_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * h->P * h->R, h->stream), "memset");
-  MAM_CUDA(cudaMemsetAsync(h->phat, 0, sizeof(double) * size_t(h->Mtot) * h->R, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->acc, 0, sizeof(unsigned long long) * MR, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->phat, 0, sizeof(double) * MR, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->diag_wc, 0, sizeof(float) * h->T, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->diag_lb, 0, sizeof(float) * h->T, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->diag_res, 0, sizeof(float) * h->T, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->iter_d, 0, sizeof(long long), h->stream), "memset");
-  MAM_CUDA(cudaMemsetAsync(h->bundle_cur, 0, sizeof(int), h->stream), "memset");
-  MAM_CUDA(cudaMemsetAsync(h->bundle_prev, 0, sizeof(int), h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->done, 0, sizeof(unsigned), h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->blk, 0, sizeof(double) * 4 * h->P * avg_blocks(h), h->stream), "memset");
   std::vector<double> ones(h->P, 1.0);
-  MAM_TRY(upload(h, h->t, ones.data(), ones.size()));
-  MAM_CUDA(cudaMemsetAsync(h->stat, 0, sizeof(double) * 4 * h->P, h->stream), "memset");
+  MAM_TRY(upload(h, h->t_used, ones.data(), ones.size()));
   const AvgArgs aa = avg_args(h, 0, 0);
   MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
   h->iter = 0;
@@ -622,6 +576,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
       beta[b] = s;
       tot += s;
       h->index_sets.push_back({h->col_off[m0], h->col_off[m1]});
+      h->index_meas.push_back({m0, m1});
     }
     if (!(tot > 0))
       return bail(fail(h, MAM_ERR_INVALID_ARG, "randomized MAM needs sum(alpha) > 0"));
@@ -632,6 +587,21 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
     }
   } else {
     h->index_sets.push_back({0, h->T});
+    h->index_meas.push_back({0, h->Mtot});
+  }
+  // Fixed-point scale of the row-sum accumulators: every sum of pi-hat over
+  // a row is at most the measure's mass, so Qmax * 2^e <= 2^61 cannot
+  // overflow the signed 64-bit accumulators.
+  {
+    double qmax = 0;
+    for (int m = 0; m < h->Mtot; ++m) {
+      double Q = 0;
+      for (long long c = h->col_off[m]; c < h->col_off[m + 1]; ++c) Q += q64[c];
+      qmax = std::max(qmax, Q);
+    }
+    int e2 = 61 - int(std::ceil(std::log2(qmax * 1.0001)));
+    e2 = std::max(0, std::min(100, e2));
+    h->fx_scale = std::ldexp(1.0, e2);
   }
 
   // Device buffers.
@@ -653,12 +623,13 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->lam, size_t(h->T), "thresholds");
   ALLOC(h->pm, MR, "marginals");
   ALLOC(h->delta, MR, "shifts");
+  ALLOC(h->acc, MR, "row-sum accumulators");
   ALLOC(h->phat, MR, "pi-hat marginals");
   ALLOC(h->p, size_t(h->P) * h->R, "barycenters");
-  ALLOC(h->t, size_t(h->P), "t");
+  ALLOC(h->t_used, size_t(h->P), "t");
   ALLOC(h->blk, size_t(h->P) * avg_blocks(h) * 4, "block sums");
-  ALLOC(h->counter, size_t(h->P), "counters");
-  ALLOC(h->stat, size_t(h->P) * 4, "statistics");
+  ALLOC(h->done, 1, "arrival counter");
+  ALLOC(h->nact, size_t(h->T), "active-set sizes");
   ALLOC(h->diag_wc, size_t(h->T), "diagnostics");
   ALLOC(h->diag_lb, size_t(h->T), "diagnostics");
   ALLOC(h->diag_res, size_t(h->T), "diagnostics");
@@ -671,6 +642,8 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->a_d, size_t(h->Mtot), "weights a");
   ALLOC(h->alpha_d, size_t(h->Mtot), "alpha");
   ALLOC(h->S_d, size_t(h->Mtot), "sizes");
+  ALLOC(h->Sd_d, size_t(h->Mtot), "sizes");
+  ALLOC(h->invS_d, size_t(h->Mtot), "sizes");
   ALLOC(h->prob_meas_d, size_t(h->P) + 1, "problem table");
   ALLOC(h->rho_d, size_t(h->P), "rho");
   ALLOC(h->gamma_d, size_t(h->P), "gamma");
@@ -679,8 +652,6 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->col_meas, size_t(h->T), "column table");
   ALLOC(h->bundle_cum_d, std::max<size_t>(1, h->bundle_cum.size()), "bundle table");
   ALLOC(h->iter_d, 1, "iteration counter");
-  ALLOC(h->bundle_cur, 1, "bundle");
-  ALLOC(h->bundle_prev, 1, "bundle");
 #undef ALLOC
 
   std::vector<float> rho_m(h->Mtot), irho_m(h->Mtot);
@@ -696,6 +667,16 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   if ((s = upload(h, h->a_d, h->a.data(), h->a.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->alpha_d, alpha_m.data(), alpha_m.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->S_d, h->S.data(), h->S.size())) != MAM_OK) return bail(s);
+  {
+    std::vector<double> Sd(h->Mtot), iS(h->Mtot);
+    for (int m = 0; m < h->Mtot; ++m) {
+      Sd[m] = double(h->S[m]);
+      iS[m] = 1.0 / double(h->S[m]);
+    }
+    if ((s = upload(h, h->Sd_d, Sd.data(), Sd.size())) != MAM_OK) return bail(s);
+    // (pageable sources: the copy has taken the data when the call returns)
+    if ((s = upload(h, h->invS_d, iS.data(), iS.size())) != MAM_OK) return bail(s);
+  }
   if ((s = upload(h, h->prob_meas_d, h->prob_meas.data(), h->prob_meas.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->rho_d, h->rho.data(), h->rho.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->gamma_d, h->gamma.data(), h->gamma.size())) != MAM_OK) return bail(s);
@@ -705,7 +686,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   if (!h->bundle_cum.empty() &&
       (s = upload(h, h->bundle_cum_d, h->bundle_cum.data(), h->bundle_cum.size())) != MAM_OK)
     return bail(s);
-  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * h->P, h->stream);
+  e = cudaMemsetAsync(h->done, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->passes, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err_d, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
@@ -833,28 +814,36 @@ mam_status mam_step(mam_problem* h, int32_t n_iters) {
 static mam_status objective_all(mam_problem* h, std::vector<mam_objective_t>& out) {
   MAM_TRY(sync(h));
   MAM_CUDA(launch_diag_reduce(h->diag_wc, h->diag_lb, h->diag_res, h->prob_cols_d,
-                              h->sched_d, h->nb > 1 ? h->bundle_prev : nullptr, h->P,
-                              h->diag_out, h->stream),
+                              h->sched_d, draw_args(h), h->iter_d, h->P, h->diag_out,
+                              h->stream),
            "diagnostic reduction");
-  std::vector<double> sums(size_t(h->P) * 3), stat(size_t(h->P) * 4), t(h->P);
+  const int nblk = avg_blocks(h);
+  std::vector<double> sums(size_t(h->P) * 3), blk(size_t(h->P) * nblk * 4), t(h->P);
   unsigned long long passes = 0;
   MAM_CUDA(cudaMemcpyAsync(sums.data(), h->diag_out, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream), "read");
-  MAM_CUDA(cudaMemcpyAsync(stat.data(), h->stat, sizeof(double) * stat.size(), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_CUDA(cudaMemcpyAsync(blk.data(), h->blk, sizeof(double) * blk.size(), cudaMemcpyDeviceToHost, h->stream), "read");
   MAM_CUDA(cudaMemcpyAsync(&passes, h->passes, sizeof(passes), cudaMemcpyDeviceToHost, h->stream), "read");
-  MAM_CUDA(cudaMemcpyAsync(t.data(), h->t, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_CUDA(cudaMemcpyAsync(t.data(), h->t_used, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, h->stream), "read");
   MAM_TRY(sync(h));
   out.resize(h->P);
   for (int i = 0; i < h->P; ++i) {
     mam_objective_t& o = out[i];
+    double e = 0, eh = 0, dp = 0;
+    for (int b = 0; b < nblk; ++b) {
+      e += blk[(size_t(i) * nblk + b) * 4];
+      eh += blk[(size_t(i) * nblk + b) * 4 + 1];
+      dp += blk[(size_t(i) * nblk + b) * 4 + 2];
+    }
     o.w_hat = sums[3 * i];
     o.lower_bound = sums[3 * i + 1];
     o.fp_resid = std::sqrt(sums[3 * i + 2]);
-    o.dist_pihat = stat[4 * i + 1];
+    o.dist_pihat = std::sqrt(eh);
     o.f_unbal = o.w_hat + (std::isinf(h->gamma[i]) ? 0.0 : h->gamma[i] * o.dist_pihat);
-    o.dp_norm = stat[4 * i + 2];
-    o.t = stat[4 * i + 3];
-    o.dist_theta = stat[4 * i];
-    o.t_next = t[i];
+    o.dp_norm = std::sqrt(dp);
+    o.t = t[i];
+    o.dist_theta = std::sqrt(e);
+    const double rD = h->rho[i] * o.dist_theta;
+    o.t_next = (std::isinf(h->gamma[i]) || rD <= h->gamma[i]) ? 1.0 : h->gamma[i] / rD;
     o.iter = h->diag_iter;
     o.newton_passes = (int64_t)passes;
   }
@@ -975,12 +964,13 @@ std::vector<Piece> state_pieces(mam_problem* h) {
   const size_t MR = size_t(h->Mtot) * h->R;
   return {{h->theta, sizeof(float) * size_t(h->T) * h->ld},
           {h->lam, sizeof(float) * size_t(h->T)},
+          {h->nact, sizeof(float) * size_t(h->T)},
           {h->pm, sizeof(double) * MR},
           {h->p, sizeof(double) * size_t(h->P) * h->R},
           {h->delta, sizeof(double) * MR},
           {h->phat, sizeof(double) * MR},
-          {h->t, sizeof(double) * h->P},
-          {h->stat, sizeof(double) * 4 * h->P},
+          {h->t_used, sizeof(double) * h->P},
+          {h->blk, sizeof(double) * 4 * size_t(h->P) * avg_blocks(h)},
           {h->diag_wc, sizeof(float) * size_t(h->T)},
           {h->diag_lb, sizeof(float) * size_t(h->T)},
           {h->diag_res, sizeof(float) * size_t(h->T)},
@@ -1010,8 +1000,6 @@ mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes) {
   hd.Mtot = h->Mtot;
   hd.R = h->R;
   hd.ld = h->ld;
-  MAM_CUDA(cudaMemcpy(&hd.bundle_cur, h->bundle_cur, sizeof(int), cudaMemcpyDeviceToHost), "state");
-  MAM_CUDA(cudaMemcpy(&hd.bundle_prev, h->bundle_prev, sizeof(int), cudaMemcpyDeviceToHost), "state");
   char* out = static_cast<char*>(buf);
   std::memcpy(out, &hd, sizeof(hd));
   size_t off = sizeof(hd);
@@ -1042,8 +1030,6 @@ mam_status mam_set_state(mam_problem* h, const void* buf, size_t bytes) {
     MAM_CUDA(cudaMemcpy(p.dev, in + off, p.bytes, cudaMemcpyHostToDevice), "state");
     off += p.bytes;
   }
-  MAM_CUDA(cudaMemcpy(h->bundle_cur, &hd.bundle_cur, sizeof(int), cudaMemcpyHostToDevice), "state");
-  MAM_CUDA(cudaMemcpy(h->bundle_prev, &hd.bundle_prev, sizeof(int), cudaMemcpyHostToDevice), "state");
   h->iter = hd.iter;
   h->diag_iter = hd.diag_iter;
   return MAM_OK;

@@ -14,13 +14,6 @@ namespace mam {
 constexpr int kGraphIters = 10;  // iterations per captured CUDA graph
 constexpr int kMaxR = 12288;     // largest column a CTA covers (threads*vec*4)
 
-struct SchedHost {
-  std::vector<int> cta_seg_begin;
-  std::vector<int4> segs;
-  std::vector<int> slot_begin, slot_end;
-  long long col_begin = 0, col_end = 0;
-};
-
 struct BackwardState;  // mam_backward.cu
 
 }  // namespace mam
@@ -52,6 +45,8 @@ struct mam_problem {
   std::vector<double> rho, gamma, Qa;   // [P]
   std::vector<double> bundle_cum;       // [nb]
   std::vector<std::pair<long long, long long>> index_sets;  // column ranges
+  std::vector<std::pair<int, int>> index_meas;              // measure ranges
+  double fx_scale = 1.0;                // 2^e of the fixed-point row sums
   std::vector<double> xi_h;             // [P][R][dim]
   std::vector<double> zeta_kept;        // [T][dim] (when available)
 
@@ -66,10 +61,10 @@ struct mam_problem {
   double* delta = nullptr;
   double* phat = nullptr;
   double* p = nullptr;
-  double* t = nullptr;
+  double* t_used = nullptr;
+  float* nact = nullptr;
+  unsigned* done = nullptr;
   double* blk = nullptr;
-  unsigned* counter = nullptr;
-  double* stat = nullptr;
   float* diag_wc = nullptr;
   float* diag_lb = nullptr;
   float* diag_res = nullptr;
@@ -82,6 +77,8 @@ struct mam_problem {
   double* a_d = nullptr;
   double* alpha_d = nullptr;
   int* S_d = nullptr;
+  double* Sd_d = nullptr;
+  double* invS_d = nullptr;
   int* prob_meas_d = nullptr;
   double* rho_d = nullptr;
   double* gamma_d = nullptr;
@@ -90,10 +87,7 @@ struct mam_problem {
   int* col_meas = nullptr;
   double* bundle_cum_d = nullptr;
   long long* iter_d = nullptr;
-  int* bundle_cur = nullptr;
-  int* bundle_prev = nullptr;
-  float* partials = nullptr;
-  int max_slots = 0;
+  unsigned long long* acc = nullptr;
 
   // schedules and launch configuration
   std::vector<void*> sched_allocs;
@@ -144,6 +138,7 @@ mam_kernel_config default_config(const mam_problem* h);
 mam_status run_iterations(mam_problem* h, int n, bool diag_last);
 mam_status launch_iteration(mam_problem* h, bool diag);
 mam_status sync(mam_problem* h);
+Draw draw_args(const mam_problem* h);
 ColArgs col_args(const mam_problem* h);
 AvgArgs avg_args(const mam_problem* h, int reduce, int diag);
 int avg_blocks(const mam_problem* h);

@@ -7,37 +7,50 @@
 
 namespace mam {
 
-// Work schedule of one index set M^k (all measures, or one bundle of
-// Remark 2).  The index set's columns are contiguous in the global column
-// order; CTA b of the persistent grid takes a contiguous slice of them.  The
-// slice is cut at measure boundaries into segments; each segment owns one
-// row of the partial row-sum buffer ("slot").  Slots of one measure are
-// consecutive, so Step 3 (p^(m) = row sums of theta^(m)) sums
-// partials[slot_begin[m] .. slot_end[m]) in a fixed order.
+// One index set M^k (all measures, or one bundle of Remark 2): its columns
+// and its measures are contiguous.  CTA b of the persistent grid of G CTAs
+// takes columns [col_begin + n*b/G, col_begin + n*(b+1)/G), n = col_end -
+// col_begin.
 struct Sched {
-  const int* cta_seg_begin;  // [G+1] first segment of each CTA
-  const int4* segs;          // [nseg] (measure, col_begin, col_end, slot)
-  const int* slot_begin;     // [Mtot] first slot of measure m (or 0)
-  const int* slot_end;       // [Mtot] one past the last slot (== begin: none)
-  long long col_begin;       // index set's first column
-  long long col_end;         // one past its last column
+  long long col_begin;
+  long long col_end;
+  int meas_begin;
+  int meas_end;
 };
 
-// Arguments of the fused column kernel (Algorithm 1, Step 2 + Step 3
-// partials, plus the fused diagnostics).
+// Remark 2 draws: the index set of column step k is a pure function of
+// (seed, k), so every kernel that needs it recomputes it from the device
+// iteration counter.
+struct Draw {
+  int nb;                    // bundles (<= 1: deterministic, index set 0)
+  const double* cum;         // [nb] cumulative probabilities
+  unsigned long long seed;
+};
+
+// Arguments of the fused column kernel (Algorithm 1, Step 2, the Step 3
+// accumulation of row sums, t^k, and the fused diagnostics).
 struct ColArgs {
   float* theta;              // [T][ld] plans, column-contiguous
   const void* cost;          // [T][ld] costs (float / bf16 / half)
   const float* q;            // [T] kept weights q_s (the simplex masses)
   float* lam;                // [T] last threshold lambda_s (NaN: none)
+  float* nact;               // [T] active-set size at that threshold (0: none)
+  const int* col_meas;       // [T] measure of each column
   const double* delta;       // [Mtot][R] (p - p^(m)) / S_m
-  const double* t;           // [P] t^k
+  const double* blk;         // [P][nblk][4] averaging block sums (dist^2 in [0])
+  int nblk;
+  const double* rho_p;       // [P]
+  const double* gamma_p;     // [P] (inf = balanced)
+  double* t_used;            // [P] t^k used by this step (written)
   const int* meas_prob;      // [Mtot] problem of each measure
   const float* rho;          // [Mtot] rho of the measure's problem
   const float* inv_rho;      // [Mtot] 1/rho
-  float* partials;           // [nslot][ld] row sums of the new theta
-  const Sched* sched;        // [n_sched] device array of schedules
-  const int* bundle_cur;     // index of the schedule to run (device), or null
+  unsigned long long* acc;   // [Mtot][R] fixed-point row sums of pi-hat
+  float fx_scale;            // fixed-point scale 2^e of acc
+  const Sched* sched;        // [n_sched] index sets (device)
+  Draw draw;
+  long long* iter;           // [1] completed column steps (advanced here)
+  unsigned* done;            // [1] CTA arrival counter (self-resetting)
   float* diag_wc;            // [T] sum_r c_rs pi-hat_rs          (DIAG)
   float* diag_lb;            // [T] q_s * min_r (c_rs - rho d_r)  (DIAG)
   float* diag_res;           // [T] sum_r (theta'_rs - theta_rs)^2 (DIAG)
@@ -49,36 +62,31 @@ struct ColArgs {
   int bisect_depth;          // bisection steps on a cold start
 };
 
-// Arguments of the averaging kernel (Algorithm 1, Step 1, t^k, and Step 3
-// reduction of the partial row sums).
+// Arguments of the averaging kernel (Algorithm 1, Step 3 completion, Step 1
+// and the distance that fixes t^k).
 struct AvgArgs {
-  int P, R, ld;
+  int P, R;
   const int* prob_meas;      // [P+1] first measure of each problem
-  const int* S;              // [Mtot] pruned support sizes
+  const double* Sd;          // [Mtot] pruned support sizes S_m
+  const double* inv_S;       // [Mtot] 1 / S_m
   const double* a;           // [Mtot] averaging weights of eq. (pr)
-  const double* rho;         // [P]
-  const double* gamma;       // [P] (inf = balanced)
-  const float* partials;
+  unsigned long long* acc;   // [Mtot][R] fixed-point sums of pi-hat (zeroed here)
+  double fx_inv_scale;       // 2^-e
   const Sched* sched;
-  const int* bundle_cur;     // bundle of the column step just done (or null)
-  int* bundle_prev;          // receives that bundle (or null)
-  int reduce;                // 1: p^(m) from partials; 0: p^(m) given
+  Draw draw;
+  const long long* iter;     // [1] completed column steps
+  const double* t_used;      // [P] t of the column step just done
+  int reduce;                // 1: p^(m) from acc; 0: p^(m) given
   int diag;                  // 1: also pi-hat marginals and their distance
   double* pm;                // [Mtot][R]
   double* p;                 // [P][R]
   double* delta;             // [Mtot][R]
   double* phat;              // [Mtot][R] row sums of pi-hat (DIAG)
-  double* t;                 // [P] in: t of the step done; out: next t
-  double* blk;               // [P][nblk][4] block partial sums
-  unsigned* counter;         // [P] arrival counters (self-resetting)
-  double* stat;              // [P][4] (dist_L(theta), dist_L(pi-hat), ||dp||, t used)
-  // Remark 2 (single randomized problem; nb <= 1 otherwise)
-  int nb;
-  const double* bundle_cum;  // [nb] cumulative draw probabilities
-  unsigned long long seed;
-  long long* iter;           // [1] completed column steps
-  int* bundle_next;          // [1] bundle of the next column step
+  double* blk;               // [P][nblk][4] block sums: dist^2, dist_hat^2, |dp|^2
 };
+
+constexpr int kAvgRows = 16;    // rows per averaging block
+constexpr int kAvgSlices = 8;   // measure slices per averaging block
 
 // Launch helpers (mam_kernels.cu).
 cudaError_t launch_column(int nv, int cost_dtype, bool diag, int grid, int threads,
@@ -93,18 +101,19 @@ cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const int* col_meas, const double* alpha,
                               long long col0, long long ncols, int R, int ld,
                               int dim, cudaStream_t st);
-cudaError_t launch_init_theta(float* theta, float* lam, const double* q,
+cudaError_t launch_init_theta(float* theta, float* lam, float* nact, const double* q,
                               long long T, int R, int ld, int mode,
                               cudaStream_t st);
 cudaError_t launch_rowsum(const float* theta, const long long* col_off,
                           int Mtot, int R, int ld, double* pm, cudaStream_t st);
 cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                const float* res, const long long* prob_cols,
-                               const Sched* sched, const int* bundle_prev,
-                               int P, double* out, cudaStream_t st);
+                               const Sched* sched, Draw draw,
+                               const long long* iter, int P, double* out,
+                               cudaStream_t st);
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
-                      const double* delta, const double* t,
+                      const double* delta, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
                       float* diag_lb, cudaStream_t st);

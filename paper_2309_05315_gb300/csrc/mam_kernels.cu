@@ -2,10 +2,11 @@
 // Marginals (arXiv 2309.05315, Algorithm 1) for sm_103a.
 //
 //   column_kernel   Step 2 of Algorithm 1 for every column of the index set
-//                   M^k, fused with the partial row sums of Step 3 and with
-//                   the diagnostics (W-hat, lower bound, fixed-point residual).
-//   average_kernel  Step 3 reduction of those partials (deterministic, FP64),
-//                   Step 1 (p = sum_m a_m p^(m), eq. pr) and the factor t^k.
+//                   M^k, fused with the row sums of Step 3 (order-independent
+//                   fixed-point accumulation) and with the diagnostics
+//                   (W-hat, lower bound, fixed-point residual).
+//   average_kernel  Step 3 completion (FP64), Step 1 (p = sum_m a_m p^(m),
+//                   eq. pr) and the factor t^k.
 //
 // Plans theta and costs c are stored column-contiguous with a padded stride
 // ld (a multiple of 8 elements), so that one column is one contiguous run of
@@ -146,14 +147,17 @@ __device__ __forceinline__ void reduce3(float& a, float& b, float& c,
     const float cc = __shfl_xor_sync(0xffffffffu, c, o);
     c = kMin ? fminf(c, cc) : fmaxf(c, cc);
   }
+  if (nw == 1) return;
   if (lane == 0) red[rb * kRedSlots + warp] = make_float4(a, b, c, 0.f);
   __syncthreads();
-  float4 r = red[rb * kRedSlots];
-  for (int i = 1; i < nw; ++i) {
-    const float4 x = red[rb * kRedSlots + i];
-    r.x += x.x;
-    r.y += x.y;
-    r.z = kMin ? fminf(r.z, x.z) : fmaxf(r.z, x.z);
+  const float ident = kMin ? INFINITY : -INFINITY;
+  float4 r = lane < nw ? red[rb * kRedSlots + lane] : make_float4(0.f, 0.f, ident, 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+    r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+    const float cc = __shfl_xor_sync(0xffffffffu, r.z, o);
+    r.z = kMin ? fminf(r.z, cc) : fmaxf(r.z, cc);
   }
   a = r.x;
   b = r.y;
@@ -169,28 +173,90 @@ struct MaxThreads {
 
 // ------------------------------------------------------- column kernel
 
+// ------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Index set of column step k (Remark 2): bundle i is drawn with probability
+// beta_i from u_k = (SplitMix64(seed + (k+1) * 0x9E3779B97F4A7C15) >> 11)
+// * 2^-53.  Deterministic MAM (nb <= 1) always uses index set 0.
+__device__ __forceinline__ int draw_index_set(const Draw& d, long long k) {
+  if (d.nb <= 1) return 0;
+  unsigned long long z = d.seed + (unsigned long long)k * 0x9E3779B97F4A7C15ull;
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const double u = double(z >> 11) * (1.0 / 9007199254740992.0);
+  int i = 0;
+  while (i < d.nb - 1 && !(u < d.cum[i])) ++i;
+  return i;
+}
+
+// t^k of Algorithm 1 from the averaging kernel's block sums of
+// sum_m ||p - p^(m)||^2 / S_m:  D = sqrt(sum), t = 1 if gamma = inf or
+// rho D <= gamma, else gamma / (rho D).  Every CTA of the column kernel
+// evaluates it with the same thread count and the same summation order, so
+// all of them obtain the same t.  Uses dred[0..31]; all threads must call.
+__device__ double t_from_blocks(const double* blk, int nblk, double rho,
+                                double gamma, double* dred, int tid, int nt) {
+  double acc = 0.0;
+  for (int i = tid; i < nblk; i += nt) acc += blk[4 * i];
+  acc = warp_sum_d(acc);
+  if ((tid & 31) == 0) dred[tid >> 5] = acc;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < (nt >> 5); ++w) tot += dred[w];
+  __syncthreads();
+  const double D = sqrt(tot);
+  if (isinf(gamma) || rho * D <= gamma) return 1.0;
+  return gamma / (rho * D);
+}
+
+// ------------------------------------------------------- column kernel
+
 // Step 2 of Algorithm 1 for one CTA's slice of the index set, one column at
 // a time.  Thread `tid` owns the float4 groups idx = v*nt + tid (v < NV) of
-// every column, i.e. rows r = 4*idx .. 4*idx+3; its shift d^(m)_r and its
-// partial row sums stay in registers for all columns of a measure.
+// every column, i.e. rows r = 4*idx .. 4*idx+3; its shift d^(m)_r stays in
+// registers while consecutive columns belong to the same measure.
 //
 // Per column s of measure m (tau = q_s):
 //   w_r     = theta_rs + 2 d_r - c_rs / rho        (Alg. 1, w)
 //   lambda  : sum_r max(w_r - lambda, 0) = tau     (Prop. 3, Remark 1)
 //   pihat_r = max(w_r - lambda, 0)                 (Alg. 1, projection)
 //   theta'  = pihat_r - d_r                        (Alg. 1, update)
-// with d_r = t^k (p_r - p^(m)_r) / S_m.
+// with d_r = t^k (p_r - p^(m)_r) / S_m.  Step 3 needs the row sums of
+// theta', i.e. sum_s pihat_rs - S_m d_r; the kernel accumulates the sparse
+// part sum_s pihat_rs as 64-bit fixed-point integers (pihat * 2^e, added with
+// integer atomics, so the result does not depend on the order of the adds).
 //
 // Threshold search (exact).  f(l) = sum_r max(w_r - l, 0) is convex,
 // piecewise linear and decreasing; n(l) = #{w_r > l} = -f'(l).  The Newton
 // step l <- l + (f(l) - tau) / n(l) equals Michelot's update
-// (sum_{w>l} w - tau) / n(l): from any l > lambda* it lands in
-// [lambda_prev_set, lambda*], and from below it increases monotonically.  The
-// active sets {w > l} of two successive iterates are nested, so equal counts
-// mean equal sets, and then the iterate is exactly lambda*.  The search
-// starts from the column's previous threshold (warm start); without one it
-// brackets lambda* in [max w - tau, max w), bisects bisect_depth times and
-// continues from the lower end.
+// (sum_{w>l} w - tau) / n(l): from any l > lambda* it lands at or below
+// lambda*, and from below it increases monotonically.  The active sets
+// {w > l} of two successive iterates are nested, so equal counts mean equal
+// sets, and then the later iterate is exactly lambda*.  The search starts
+// from the column's previous threshold (warm start); without one it brackets
+// lambda* in [max w - tau, max w), bisects bisect_depth times and continues
+// from the lower end.
+//
+// Schedule of one column (warm start, the common case).  Pass 1 builds w and
+// evaluates (f, n) at the previous threshold l0.  The Newton iterate
+// l1 = l0 + (f - tau)/n satisfies l1 >= l0 - tau/n, so rows with
+// w <= l0 - tau/n can neither count in (f, n)(l1) nor be active at the
+// answer; pass 1 marks the float4 groups holding a row above
+// lc = l0 - 1.5 tau/n_prev (n_prev: the column's last active-set size) and
+// pass 2, at l1, visits only groups some lane of the warp marked (a
+// warp-uniform vote), computing the projection and theta' there.  When
+// l1 < lc (the guess n_prev was off) pass 2 visits everything.  Equal counts
+// in pass 1 and pass 2 confirm the active set and the registers are stored.
+// Two CTA-wide reductions per column; the shared-memory stage returns to
+// the copy engine right after the first.
 template <int NV, typename CT, bool DIAG>
 __global__ void __launch_bounds__(MaxThreads<NV>::value)
     column_kernel(const ColArgs A) {
@@ -210,370 +276,433 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
   uint64_t* bar = reinterpret_cast<uint64_t*>(
       smem + size_t(stages) * ld * (sizeof(float) + sizeof(CT)));
   float4* red = reinterpret_cast<float4*>(bar + 4);
+  double* dred = reinterpret_cast<double*>(red + 2 * kRedSlots);
 
-  const int bundle = A.bundle_cur ? *A.bundle_cur : 0;
-  const Sched sc = A.sched[bundle];
-  const int sb = sc.cta_seg_begin[blockIdx.x];
-  const int se = sc.cta_seg_begin[blockIdx.x + 1];
-  if (sb >= se) return;  // uniform over the CTA
-  int4 sg = sc.segs[sb];
-  const long long col0 = sg.y;
-  const long long ncol = (long long)sc.segs[se - 1].z - col0;
-
-  const uint32_t bytes_th = uint32_t(ld) * sizeof(float);
-  const uint32_t bytes_c = uint32_t(ld) * sizeof(CT);
-  if (tid == 0) {
-    for (int s = 0; s < stages; ++s) mbar_init(&bar[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  long long issued = 0;  // meaningful in thread 0 only
-  auto issue = [&](long long j) {
-    const int s = int(j % stages);
-    const long long col = col0 + j;
-    mbar_expect_tx(&bar[s], bytes_th + bytes_c);
-    bulk_load(th_s + size_t(s) * ld, A.theta + size_t(col) * ld, bytes_th,
-              &bar[s]);
-    bulk_load(c_s + size_t(s) * ld,
-              static_cast<const CT*>(A.cost) + size_t(col) * ld, bytes_c,
-              &bar[s]);
-  };
-  if (tid == 0) {
-    const long long n0 = ncol < stages ? ncol : stages;
-    for (long long j = 0; j < n0; ++j) issue(j);
-    issued = n0;
-  }
-
-  float d[NV][4];
-  float part[NV][4];
-  float rho_m = 0.f, irho_m = 0.f;
-  auto setup = [&](int m) {
-    const double tt = A.t[A.meas_prob[m]];
-    rho_m = A.rho[m];
-    irho_m = A.inv_rho[m];
-    const double* dl = A.delta + size_t(m) * R;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int idx = v * nt + tid;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = 4 * idx + e;
-        d[v][e] = (idx < ld4 && r < R) ? float(tt * dl[r]) : 0.f;
-        part[v][e] = 0.f;
-      }
-    }
-  };
-  auto flush = [&](int slot) {
-    float4* dst = reinterpret_cast<float4*>(A.partials + size_t(slot) * ld);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int idx = v * nt + tid;
-      if (idx < ld4)
-        dst[idx] = make_float4(part[v][0], part[v][1], part[v][2], part[v][3]);
-    }
-  };
-  setup(sg.x);
-
-  int rb = 0;
-  unsigned long long my_passes = 0;
-  bool failed = false;
+  const long long k_iter = *A.iter;
+  const Sched sc = A.sched[draw_index_set(A.draw, k_iter)];
+  const long long n_all = sc.col_end - sc.col_begin;
+  const long long G = gridDim.x;
+  const long long col0 = sc.col_begin + n_all * blockIdx.x / G;
+  const long long ncol = sc.col_begin + n_all * (blockIdx.x + 1) / G - col0;
   bool any_fail = false;
-  int seg = sb;
-  for (long long j = 0; j < ncol; ++j) {
-    const long long col = col0 + j;
-    if (col >= sg.z) {  // next measure inside this CTA's slice
-      flush(sg.w);
-      ++seg;
-      sg = sc.segs[seg];
-      setup(sg.x);
+  unsigned long long my_passes = 0;
+
+  if (ncol > 0) {  // uniform over the CTA
+    const uint32_t bytes_th = uint32_t(ld) * sizeof(float);
+    const uint32_t bytes_c = uint32_t(ld) * sizeof(CT);
+    if (tid == 0) {
+      for (int s = 0; s < stages; ++s) mbar_init(&bar[s], 1);
+      fence_mbar_init();
     }
-    const int s = int(j % stages);
-    if (!mbar_wait_bounded(&bar[s], uint32_t((j / stages) & 1), kWaitLimitNs))
-      failed = true;  // keep control flow uniform; checked below
-
-    const float tau = A.q[col];
-    float lam = A.lam[col];
-    const float* ths = th_s + size_t(s) * ld;
-    const CT* cs = c_s + size_t(s) * ld;
-
-    float w[NV][4];
-    float lbmin = INFINITY;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int idx = v * nt + tid;
-      if (idx < ld4) {
-        const float4 th = reinterpret_cast<const float4*>(ths)[idx];
-        const float4 c = CostIO<CT>::load4(cs, idx);
-        const float thv[4] = {th.x, th.y, th.z, th.w};
-        const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const bool ok = 4 * idx + e < R;
-          w[v][e] = ok ? (thv[e] + 2.f * d[v][e]) - cv[e] * irho_m : -INFINITY;
-          if (DIAG && ok) lbmin = fminf(lbmin, cv[e] - rho_m * d[v][e]);
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) w[v][e] = -INFINITY;
-      }
+    __syncthreads();
+    long long issued = 0;  // meaningful in thread 0 only
+    auto issue = [&](long long j) {
+      const int s = int(j % stages);
+      const long long col = col0 + j;
+      mbar_expect_tx(&bar[s], bytes_th + bytes_c);
+      bulk_load(th_s + size_t(s) * ld, A.theta + size_t(col) * ld, bytes_th,
+                &bar[s]);
+      bulk_load(c_s + size_t(s) * ld,
+                static_cast<const CT*>(A.cost) + size_t(col) * ld, bytes_c,
+                &bar[s]);
+    };
+    if (tid == 0) {
+      const long long n0 = ncol < stages ? ncol : stages;
+      for (long long j = 0; j < n0; ++j) issue(j);
+      issued = n0;
     }
-
-    int np = 0;
-    if (!(tau > 0.f)) {
-      lam = INFINITY;  // Remark 1: the projection onto Delta_R(0) is 0
-    } else {
-      float nprev = -1.f;
-      bool need_max = true;
-      if (!(lam == lam)) {  // no previous threshold: bracket and bisect
-        float mx = -INFINITY;
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) mx = fmaxf(mx, w[v][e]);
-        float z0 = 0.f, z1 = 0.f;
-        reduce3<false>(z0, z1, mx, red, rb, lane, warp, nw);
-        ++np;
-        float lo = mx - tau, hi = mx;
-        for (int b = 0; b < A.bisect_depth; ++b) {
-          const float mid = 0.5f * (lo + hi);
-          float f = 0.f, n = 0.f, z = 0.f;
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) f += fmaxf(w[v][e] - mid, 0.f);
-          reduce3<false>(f, n, z, red, rb, lane, warp, nw);
-          ++np;
-          if (f >= tau) lo = mid; else hi = mid;
-        }
-        lam = lo;
-        need_max = false;
+    // Thread 0 refills the stage of column j with column j + stages, once
+    // every thread is past its last read of that stage.
+    auto refill = [&](long long j) {
+      if (tid == 0 && j + stages < ncol) {
+        issue(j + stages);
+        ++issued;
       }
-      for (int it = 0; it < kMaxNewton; ++it) {
-        float f = 0.f, n = 0.f, mx = -INFINITY;
-        if (need_max) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float x = w[v][e] - lam;
-              f += fmaxf(x, 0.f);
-              n += x > 0.f ? 1.f : 0.f;
-              mx = fmaxf(mx, w[v][e]);
-            }
-        } else {
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float x = w[v][e] - lam;
-              f += fmaxf(x, 0.f);
-              n += x > 0.f ? 1.f : 0.f;
-            }
-        }
-        reduce3<false>(f, n, mx, red, rb, lane, warp, nw);
-        ++np;
-        if (n == nprev) {  // same active set twice: lam is the threshold
-          lam = lam + (f - tau) / n;
-          break;
-        }
-        if (n == 0.f) {  // warm start above max w: restart from below
-          lam = mx - tau;
-          nprev = -1.f;
-          need_max = false;
-          continue;
-        }
-        lam = lam + (f - tau) / n;
-        nprev = n;
-        need_max = false;
-      }
-    }
+    };
 
-    // Projection, theta update, partial row sums (+ diagnostics).
-    float wc = 0.f, res = 0.f;
-    float4* gth = reinterpret_cast<float4*>(A.theta + size_t(col) * ld);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int idx = v * nt + tid;
-      if (idx < ld4) {
-        float o[4];
-        float pv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          pv[e] = fmaxf(w[v][e] - lam, 0.f);
-          o[e] = pv[e] - d[v][e];
-          part[v][e] += o[e];
+    float d[NV][4];
+    float rho_m = 0.f, irho_m = 0.f;
+    int m_cur = -1, p_cur = -1;
+    double t_cur = 1.0;
+    unsigned long long* acc_m = nullptr;
+    const float fx = A.fx_scale;
+    int rb = 0;
+
+    // Per-column scalars are loaded one column ahead.
+    int m_nx = A.col_meas[col0];
+    float tau_nx = A.q[col0];
+    float lam_nx = A.lam[col0];
+    float cnt_nx = A.nact[col0];
+    for (long long j = 0; j < ncol; ++j) {
+      const long long col = col0 + j;
+      const int m = m_nx;
+      const float tau = tau_nx;
+      const float lam_prev = lam_nx;
+      const float cnt_prev = cnt_nx;
+      if (j + 1 < ncol) {
+        m_nx = A.col_meas[col + 1];
+        tau_nx = A.q[col + 1];
+        lam_nx = A.lam[col + 1];
+        cnt_nx = A.nact[col + 1];
+      }
+      if (m != m_cur) {  // first column of a measure in this slice
+        m_cur = m;
+        const int pr = A.meas_prob[m];
+        if (pr != p_cur) {
+          p_cur = pr;
+          t_cur = t_from_blocks(A.blk + size_t(pr) * A.nblk * 4, A.nblk,
+                                A.rho_p[pr], A.gamma_p[pr], dred, tid, nt);
+          if (tid == 0) A.t_used[pr] = t_cur;
         }
-        if (DIAG) {
+        rho_m = A.rho[m];
+        irho_m = A.inv_rho[m];
+        acc_m = A.acc + size_t(m) * R;
+        const double* dl = A.delta + size_t(m) * R;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int idx = v * nt + tid;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = 4 * idx + e;
+            d[v][e] = (idx < ld4 && r < R) ? float(t_cur * dl[r]) : 0.f;
+          }
+        }
+      }
+      const int s = int(j % stages);
+      const bool failed =
+          !mbar_wait_bounded(&bar[s], uint32_t((j / stages) & 1), kWaitLimitNs);
+      const float* ths = th_s + size_t(s) * ld;
+      const CT* cs = c_s + size_t(s) * ld;
+      const bool pos = tau > 0.f;
+      const bool warm = pos && (lam_prev == lam_prev);
+      const float l0 = warm ? lam_prev : 0.f;
+      // Groups that can matter at the next Newton iterate (see above).
+      const float lc = (warm && cnt_prev >= 1.f) ? l0 - 1.5f * tau / cnt_prev : -INFINITY;
+
+      // Pass 1: w, and (f, n) at l0 (max w as well when cold).
+      float w[NV][4];
+      bool mark[NV];
+      float lbmin = INFINITY;
+      float fv[NV], nv[NV];
+      float mx = -INFINITY;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        fv[v] = 0.f;
+        nv[v] = 0.f;
+        mark[v] = false;
+        const int idx = v * nt + tid;
+        if (idx < ld4) {
           const float4 th = reinterpret_cast<const float4*>(ths)[idx];
           const float4 c = CostIO<CT>::load4(cs, idx);
           const float thv[4] = {th.x, th.y, th.z, th.w};
           const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            if (4 * idx + e < R) {
-              wc += cv[e] * pv[e];
-              const float dd = o[e] - thv[e];
-              res += dd * dd;
-            }
+            const bool ok = 4 * idx + e < R;
+            const float wv = ok ? (thv[e] + 2.f * d[v][e]) - cv[e] * irho_m : -INFINITY;
+            w[v][e] = wv;
+            const float x = wv - l0;
+            fv[v] += fmaxf(x, 0.f);
+            nv[v] += x > 0.f ? 1.f : 0.f;
+            mark[v] = mark[v] || wv > lc;
+            if (!warm) mx = fmaxf(mx, wv);
+            if (DIAG && ok) lbmin = fminf(lbmin, cv[e] - rho_m * d[v][e]);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) w[v][e] = -INFINITY;
+        }
+      }
+      float f = 0.f, n = 0.f;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        f += fv[v];
+        n += nv[v];
+      }
+      // The failure flag rides in the first reduction (uniform afterwards).
+      float flag = failed ? 1.f : 0.f;
+      if (warm) {
+        reduce3<false>(f, n, flag, red, rb, lane, warp, nw);
+      } else {
+        reduce3<false>(flag, n, mx, red, rb, lane, warp, nw);
+      }
+      if (!DIAG) refill(j);
+      int np = 1;
+      any_fail = flag > 0.f;
+
+      float o[NV][4];
+      float lam_fin = INFINITY;
+      float n_fin = 0.f;
+      bool have_o = false;
+      bool sparse = false;  // o holds -d in unvisited groups
+      if (pos) {
+        float nprev = -1.f;
+        bool bracket = !warm;
+        float lam = l0;
+        if (warm) {
+          if (n == 0.f) {
+            bracket = true;  // warm start at or above max w: need max w
+          } else {
+            lam = l0 + (f - tau) / n;
+            nprev = n;
+            sparse = lam >= lc;
           }
         }
-        gth[idx] = make_float4(o[0], o[1], o[2], o[3]);
+        for (int it = 0; it < kMaxNewton; ++it) {
+          if (bracket) {  // lambda* lies in [max w - tau, max w)
+            if (warm) {   // max w was not reduced in pass 1
+              float z0 = 0.f, z1 = 0.f;
+              mx = -INFINITY;
+#pragma unroll
+              for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) mx = fmaxf(mx, w[v][e]);
+              reduce3<false>(z0, z1, mx, red, rb, lane, warp, nw);
+              ++np;
+            }
+            float lo = mx - tau, hi = mx;
+            for (int b = 0; b < A.bisect_depth; ++b) {
+              const float mid = 0.5f * (lo + hi);
+              float fb = 0.f, z = 0.f, y = 0.f;
+#pragma unroll
+              for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) fb += fmaxf(w[v][e] - mid, 0.f);
+              reduce3<false>(fb, z, y, red, rb, lane, warp, nw);
+              ++np;
+              if (fb >= tau) lo = mid; else hi = mid;
+            }
+            lam = lo;
+            nprev = -1.f;
+            bracket = false;
+            sparse = false;
+          }
+          // (f, n) at lam, with the projection computed on the way.
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            fv[v] = 0.f;
+            nv[v] = 0.f;
+            const bool visit = !sparse || __any_sync(0xffffffffu, mark[v]);
+            if (visit) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float x = w[v][e] - lam;
+                const float pv = fmaxf(x, 0.f);
+                fv[v] += pv;
+                nv[v] += x > 0.f ? 1.f : 0.f;
+                o[v][e] = pv - d[v][e];
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) o[v][e] = -d[v][e];
+            }
+          }
+          f = 0.f;
+          n = 0.f;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            f += fv[v];
+            n += nv[v];
+          }
+          float z = 0.f;
+          reduce3<false>(f, n, z, red, rb, lane, warp, nw);
+          ++np;
+          if (n == nprev) {  // same active set twice: lam is the threshold
+            have_o = true;
+            lam_fin = lam;
+            n_fin = n;
+            break;
+          }
+          sparse = false;  // later passes visit every group
+          if (n == 0.f) {  // not expected from below; restart from the bracket
+            bracket = true;
+            continue;
+          }
+          nprev = n;
+          lam = lam + (f - tau) / n;
+        }
+        if (!have_o) {  // pass budget exhausted (not expected): use the last lam
+          lam_fin = lam;
+          n_fin = nprev;
+        }
       }
-    }
-    if (DIAG) {
-      reduce3<true>(wc, res, lbmin, red, rb, lane, warp, nw);
-      if (tid == 0) {
-        A.diag_wc[col] = wc;
-        A.diag_res[col] = res;
-        A.diag_lb[col] = tau * lbmin;
-      }
-    }
-    if (tid == 0) A.lam[col] = lam;
-    my_passes += np;
 
-    any_fail = __syncthreads_or(failed) != 0;  // stage s is free after this
-    if (any_fail) break;
-    if (tid == 0 && j + stages < ncol) {
-      issue(j + stages);
-      ++issued;
+      // Commit: theta' = pihat - d, Step 3 row sums (+ diagnostics).
+      float wc = 0.f, res = 0.f;
+      float4* gth = reinterpret_cast<float4*>(A.theta + size_t(col) * ld);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int idx = v * nt + tid;
+        float pv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pv[e] = fmaxf(w[v][e] - lam_fin, 0.f);
+        if (!have_o) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) o[v][e] = pv[e] - d[v][e];
+        }
+        // pihat is sparse: convert and add only where some lane of the warp
+        // has an active row in this group.
+        const bool act = pv[0] > 0.f || pv[1] > 0.f || pv[2] > 0.f || pv[3] > 0.f;
+        if (__any_sync(0xffffffffu, act) && act && idx < ld4) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (pv[e] > 0.f)
+              atomicAdd(acc_m + 4 * idx + e,
+                        (unsigned long long)__float2ll_rn(pv[e] * fx));
+        }
+        if (idx < ld4) {
+          if (DIAG) {
+            const float4 th = reinterpret_cast<const float4*>(ths)[idx];
+            const float4 c = CostIO<CT>::load4(cs, idx);
+            const float thv[4] = {th.x, th.y, th.z, th.w};
+            const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (4 * idx + e < R) {
+                wc += cv[e] * pv[e];
+                const float dd = o[v][e] - thv[e];
+                res += dd * dd;
+              }
+            }
+          }
+          gth[idx] = make_float4(o[v][0], o[v][1], o[v][2], o[v][3]);
+        }
+      }
+      if (DIAG) {
+        reduce3<true>(wc, res, lbmin, red, rb, lane, warp, nw);
+        if (tid == 0) {
+          A.diag_wc[col] = wc;
+          A.diag_res[col] = res;
+          A.diag_lb[col] = tau * lbmin;
+        }
+        refill(j);  // the reduction's barrier ended every read of stage s
+      }
+      if (tid == 0) {
+        A.lam[col] = lam_fin;
+        A.nact[col] = n_fin;
+      }
+      my_passes += np;
+      if (any_fail) break;  // uniform: the flag went through a reduction
+    }
+    if (any_fail && tid == 0) {
+      atomicCAS(A.err, 0, 1);
+      // Drain the copies still in flight (bounded) before leaving.
+      for (long long j = 0; j < issued; ++j)
+        mbar_wait_bounded(&bar[j % stages], uint32_t((j / stages) & 1),
+                          kWaitLimitNs / 20);
     }
   }
-  if (!any_fail) {
-    flush(sg.w);
-  } else if (tid == 0) {
-    atomicCAS(A.err, 0, 1);
-    // Drain the copies still in flight (bounded) before leaving.
-    for (long long j = 0; j < issued; ++j)
-      mbar_wait_bounded(&bar[j % stages], uint32_t((j / stages) & 1),
-                        kWaitLimitNs / 20);
+  if (tid == 0) {
+    atomicAdd(A.passes, my_passes);
+    // The last CTA to finish advances the iteration counter (every CTA has
+    // read it by then).
+    __threadfence();
+    if (atomicAdd(A.done, 1u) == gridDim.x - 1) {
+      *A.iter = k_iter + 1;
+      *A.done = 0u;
+    }
   }
-  if (tid == 0) atomicAdd(A.passes, my_passes);
 }
 
 // ------------------------------------------------------ average kernel
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Step 3 (reduction of the partial row sums into p^(m), FP64, fixed order),
-// Step 1 (p = sum_m a_m p^(m)) and the factor t^k of Algorithm 1:
-//   D = sqrt(sum_m ||p - p^(m)||^2 / S_m) = dist_L(theta)   (text after Alg. 1)
-//   t = 1 if gamma = inf or rho D <= gamma, else gamma / (rho D).
-// Grid (ceil(R/256), P).  The last block of each problem to finish combines
-// the block sums (arrival counter, fixed order) and publishes t, the
-// statistics and, for Remark 2, the next bundle.
-__global__ void __launch_bounds__(256) average_kernel(const AvgArgs A) {
-  __shared__ double sred[8][4];
-  __shared__ bool is_last;
+// Step 3 completion and Step 1 of Algorithm 1, FP64:
+//   p^(m)_r = sum_s pihat_rs - S_m d_r   (row sums of theta' = pihat - d)
+//   p = sum_m a_m p^(m)                  (eq. pr)
+//   delta^(m) = (p - p^(m)) / S_m        (the next column step uses t delta)
+// and the block sums of sum_m ||p - p^(m)||^2 / S_m (dist_L(theta)^2, which
+// fixes t^k), of the same for the pi-hat marginals (diagnostics) and of
+// ||p_new - p_old||^2.  Only the measures of the index set just processed
+// get new p^(m); the others keep theirs (Remark 2).  Block
+// (kAvgRows, kAvgSlices): threadIdx.x picks the row, threadIdx.y a slice of
+// the measures (m = m0 + y + k * kAvgSlices), so loads of different measures
+// are in flight together; slices are combined in shared memory in a fixed
+// order.  Grid (ceil(R/kAvgRows), P).
+__global__ void __launch_bounds__(kAvgRows * kAvgSlices)
+    average_kernel(const AvgArgs A) {
+  __shared__ double sp[kAvgSlices][kAvgRows];
+  __shared__ double sq[kAvgSlices][kAvgRows];
+  __shared__ double sr[kAvgRows * kAvgSlices / 32][3];
   const int pr = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r = blockIdx.x * kAvgRows + tx;
   const int m0 = A.prob_meas[pr], m1 = A.prob_meas[pr + 1];
-  const double t_old = A.t[pr];
-  const int bundle = A.bundle_cur ? *A.bundle_cur : 0;
-  const Sched sc = A.sched[bundle];
-  double e = 0.0, eh = 0.0, dp2 = 0.0;
-  if (r < A.R) {
-    double p_new = 0.0;
-    for (int m = m0; m < m1; ++m) {
+  const double t_old = A.t_used[pr];
+  const Sched sc = A.sched[draw_index_set(A.draw, *A.iter - 1)];
+  const bool row = r < A.R;
+  // pass 1: new marginals of this slice's measures, partial sums of a_m p^(m)
+  double ps = 0.0, phs = 0.0;
+  if (row) {
+    for (int m = m0 + ty; m < m1; m += kAvgSlices) {
       const size_t o = size_t(m) * A.R + r;
-      if (A.reduce) {
-        const int s0 = sc.slot_begin[m], s1 = sc.slot_end[m];
-        if (s1 > s0) {
-          double acc = 0.0;
-          for (int s = s0; s < s1; ++s) acc += double(A.partials[size_t(s) * A.ld + r]);
-          if (A.diag) A.phat[o] = acc + double(A.S[m]) * t_old * A.delta[o];
-          A.pm[o] = acc;
-        }
+      double pmv;
+      if (A.reduce && m >= sc.meas_begin && m < sc.meas_end) {
+        const double sum_pihat = double((long long)A.acc[o]) * A.fx_inv_scale;
+        A.acc[o] = 0ull;
+        // the column kernel subtracted d = float(t delta) from every entry
+        const double d_used = double(float(t_old * A.delta[o]));
+        if (A.diag) A.phat[o] = sum_pihat;
+        pmv = sum_pihat - A.Sd[m] * d_used;
+        A.pm[o] = pmv;
+      } else {
+        pmv = A.pm[o];
       }
-      p_new += A.a[m] * A.pm[o];
+      ps += A.a[m] * pmv;
+      if (A.diag) phs += A.a[m] * A.phat[o];
     }
-    double ph = 0.0;
-    for (int m = m0; m < m1; ++m) {
+  }
+  sp[ty][tx] = ps;
+  sq[ty][tx] = phs;
+  __syncthreads();
+  double p_new = 0.0, ph = 0.0;
+  for (int y = 0; y < kAvgSlices; ++y) {
+    p_new += sp[y][tx];
+    ph += sq[y][tx];
+  }
+  // pass 2: shifts and the distance terms
+  double e = 0.0, eh = 0.0, dp2 = 0.0;
+  if (row) {
+    for (int m = m0 + ty; m < m1; m += kAvgSlices) {
       const size_t o = size_t(m) * A.R + r;
       const double df = p_new - A.pm[o];
-      const double sm = double(A.S[m]);
-      e += df * df / sm;
-      A.delta[o] = df / sm;
-      if (A.diag) ph += A.a[m] * A.phat[o];
-    }
-    if (A.diag) {
-      for (int m = m0; m < m1; ++m) {
-        const double df = ph - A.phat[size_t(m) * A.R + r];
-        eh += df * df / double(A.S[m]);
+      const double is = A.inv_S[m];
+      const double dfs = df * is;
+      e += df * dfs;
+      A.delta[o] = dfs;
+      if (A.diag) {
+        const double dh = ph - A.phat[o];
+        eh += dh * dh * is;
       }
     }
-    double* pp = A.p + size_t(pr) * A.R + r;
-    const double dd = p_new - *pp;
-    dp2 = dd * dd;
-    *pp = p_new;
+    if (ty == 0) {
+      double* pp = A.p + size_t(pr) * A.R + r;
+      const double dd = p_new - *pp;
+      dp2 = dd * dd;
+      *pp = p_new;
+    }
   }
   e = warp_sum_d(e);
   eh = warp_sum_d(eh);
   dp2 = warp_sum_d(dp2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int flat = ty * kAvgRows + tx;
+  const int warp = flat >> 5, lane = flat & 31;
   if (lane == 0) {
-    sred[warp][0] = e;
-    sred[warp][1] = eh;
-    sred[warp][2] = dp2;
+    sr[warp][0] = e;
+    sr[warp][1] = eh;
+    sr[warp][2] = dp2;
   }
   __syncthreads();
-  const int nblk = gridDim.x;
-  if (threadIdx.x == 0) {
+  if (flat == 0) {
     double b0 = 0, b1 = 0, b2 = 0;
-    for (int i = 0; i < int(blockDim.x >> 5); ++i) {
-      b0 += sred[i][0];
-      b1 += sred[i][1];
-      b2 += sred[i][2];
+    for (int i = 0; i < kAvgRows * kAvgSlices / 32; ++i) {
+      b0 += sr[i][0];
+      b1 += sr[i][1];
+      b2 += sr[i][2];
     }
-    double* blk = A.blk + (size_t(pr) * nblk + blockIdx.x) * 4;
+    double* blk = A.blk + (size_t(pr) * gridDim.x + blockIdx.x) * 4;
     blk[0] = b0;
     blk[1] = b1;
     blk[2] = b2;
-    __threadfence();
-    const unsigned prev = atomicAdd(A.counter + pr, 1u);
-    is_last = (prev == unsigned(nblk - 1));
-  }
-  __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
-  __threadfence();
-  double s0 = 0, s1 = 0, s2 = 0;
-  for (int i = 0; i < nblk; ++i) {
-    const volatile double* blk = A.blk + (size_t(pr) * nblk + i) * 4;
-    s0 += blk[0];
-    s1 += blk[1];
-    s2 += blk[2];
-  }
-  const double D = sqrt(s0);
-  const double rho = A.rho[pr], gamma = A.gamma[pr];
-  double t_new = 1.0;
-  if (!isinf(gamma) && !(rho * D <= gamma)) t_new = gamma / (rho * D);
-  double* st = A.stat + size_t(pr) * 4;
-  st[0] = D;
-  if (A.diag) st[1] = sqrt(s1);
-  st[2] = sqrt(s2);
-  st[3] = t_old;
-  A.t[pr] = t_new;
-  A.counter[pr] = 0u;
-  if (pr == 0 && A.iter) {
-    if (A.bundle_prev) *A.bundle_prev = bundle;
-    long long k = *A.iter;
-    if (A.reduce) k += 1;
-    *A.iter = k;
-    if (A.nb > 1) {
-      // Remark 2 draw for column step k (counter-based SplitMix64).
-      unsigned long long z = A.seed + (unsigned long long)k * 0x9E3779B97F4A7C15ull;
-      z += 0x9E3779B97F4A7C15ull;
-      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-      z ^= z >> 31;
-      const double u = double(z >> 11) * (1.0 / 9007199254740992.0);
-      int i = 0;
-      while (i < A.nb - 1 && !(u < A.bundle_cum[i])) ++i;
-      *A.bundle_next = i;
-    }
   }
 }
 
@@ -628,9 +757,10 @@ __global__ void build_cost_kernel(CT* cost, const double* xi,
 
 // theta^0 (Alg. 1 Step 0; "Initialization" leaves it arbitrary):
 // mode 0: theta_rs = q_s / R, mode 1: 0.  Padding rows are 0 and every
-// threshold starts unknown (NaN).
-__global__ void init_theta_kernel(float* theta, float* lam, const double* q,
-                                  long long T, int R, int ld, int mode) {
+// threshold starts unknown (NaN, active-set size 0).
+__global__ void init_theta_kernel(float* theta, float* lam, float* nact,
+                                  const double* q, long long T, int R, int ld,
+                                  int mode) {
   const long long n = T * ld;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -639,7 +769,10 @@ __global__ void init_theta_kernel(float* theta, float* lam, const double* q,
     float v = 0.f;
     if (mode == 0 && r < R) v = float(q[col] / double(R));
     theta[i] = v;
-    if (r == 0) lam[col] = __int_as_float(0x7fc00000);
+    if (r == 0) {
+      lam[col] = __int_as_float(0x7fc00000);
+      nact[col] = 0.f;
+    }
   }
 }
 
@@ -660,14 +793,14 @@ __global__ void rowsum_kernel(const float* theta, const long long* col_off,
 // the columns of the last index set.
 __global__ void __launch_bounds__(256) diag_reduce_kernel(
     const float* wc, const float* lb, const float* res,
-    const long long* prob_cols, const Sched* sched, const int* bundle_prev,
-    double* out) {
+    const long long* prob_cols, const Sched* sched, Draw draw,
+    const long long* iter, double* out) {
   __shared__ double sh[8][3];
   const int i = blockIdx.x;
   const long long c0 = prob_cols[i], c1 = prob_cols[i + 1];
   long long r0 = c0, r1 = c1;
-  if (bundle_prev) {
-    const Sched sc = sched[*bundle_prev];
+  if (draw.nb > 1) {
+    const Sched sc = sched[draw_index_set(draw, *iter - 1)];
     r0 = sc.col_begin > c0 ? sc.col_begin : c0;
     r1 = sc.col_end < c1 ? sc.col_end : c1;
   }
@@ -705,7 +838,7 @@ __global__ void __launch_bounds__(256) diag_reduce_kernel(
 // One warp per column.
 template <typename CT>
 __global__ void __launch_bounds__(256) lb_kernel(
-    const CT* cost, const float* q, const double* delta, const double* t,
+    const CT* cost, const float* q, const double* delta, const double* t_used,
     const int* meas_prob, const float* rho, const int* col_meas, long long T,
     int R, int ld, float* diag_lb) {
   const int lane = threadIdx.x & 31;
@@ -713,7 +846,7 @@ __global__ void __launch_bounds__(256) lb_kernel(
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long col = w0; col < T; col += nwarp) {
     const int m = col_meas[col];
-    const float tt = float(t[meas_prob[m]]);
+    const float tt = float(t_used[meas_prob[m]]);
     const float rh = rho[m];
     const double* dl = delta + size_t(m) * R;
     const CT* cc = cost + size_t(col) * ld;
@@ -822,7 +955,7 @@ cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
 }
 
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st) {
-  average_kernel<<<dim3(nblk, a.P), 256, 0, st>>>(a);
+  average_kernel<<<dim3(nblk, a.P), dim3(kAvgRows, kAvgSlices), 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -857,14 +990,14 @@ cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_theta(float* theta, float* lam, const double* q,
-                              long long T, int R, int ld, int mode,
-                              cudaStream_t st) {
+cudaError_t launch_init_theta(float* theta, float* lam, float* nact,
+                              const double* q, long long T, int R, int ld,
+                              int mode, cudaStream_t st) {
   const long long n = T * ld;
   long long g = (n + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
   if (g < 1) g = 1;
-  init_theta_kernel<<<int(g), 256, 0, st>>>(theta, lam, q, T, R, ld, mode);
+  init_theta_kernel<<<int(g), 256, 0, st>>>(theta, lam, nact, q, T, R, ld, mode);
   return cudaGetLastError();
 }
 
@@ -877,7 +1010,7 @@ cudaError_t launch_rowsum(const float* theta, const long long* col_off,
 }
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
-                      const double* delta, const double* t,
+                      const double* delta, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
                       float* diag_lb, cudaStream_t st) {
@@ -886,13 +1019,13 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
   if (g < 1) g = 1;
   switch (cost_dtype) {
     case 0:
-      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta, t, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
       break;
     case 1:
-      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta, t, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
       break;
     case 2:
-      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta, t, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -902,10 +1035,11 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
 
 cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                const float* res, const long long* prob_cols,
-                               const Sched* sched, const int* bundle_prev,
-                               int P, double* out, cudaStream_t st) {
-  diag_reduce_kernel<<<P, 256, 0, st>>>(wc, lb, res, prob_cols, sched,
-                                        bundle_prev, out);
+                               const Sched* sched, Draw draw,
+                               const long long* iter, int P, double* out,
+                               cudaStream_t st) {
+  diag_reduce_kernel<<<P, 256, 0, st>>>(wc, lb, res, prob_cols, sched, draw,
+                                        iter, out);
   return cudaGetLastError();
 }
 

@@ -160,7 +160,7 @@ def test_randomized_bundles(Mam):
 @pytest.mark.parametrize("cfg", [
     dict(threads=32, vec=2, stages=2),
     dict(threads=64, vec=1, stages=3),
-    dict(threads=32, vec=1, stages=4, ctas_per_sm=1),
+    dict(threads=32, vec=8, stages=4, ctas_per_sm=1),
     dict(threads=96, vec=1, stages=2, ctas_per_sm=2),
 ])
 def test_kernel_configurations(Mam, cfg):
