@@ -171,13 +171,30 @@ static mam_status sched_alloc(mam_problem* h, void** p, size_t bytes) {
   return MAM_OK;
 }
 
-size_t column_smem_bytes(const mam_problem* h, int stages) {
-  return size_t(stages) * h->ld * (sizeof(float) + cost_elem_size(h->cost_dtype)) +
+size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c) {
+  // Each stage holds one column padded to threads * vec * 4 elements.
+  const size_t tile = size_t(c.threads) * c.vec * 4;
+  return size_t(c.stages) * tile * (sizeof(float) + cost_elem_size(h->cost_dtype)) +
          4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4) +
          kRedSlots * sizeof(double);
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
+  if (c.stages == 0) {  // one warp per column
+    if (!warp_kernel_has(c.vec))
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "warp kernel: vec must be one of 1,2,4,7,8,13,16,24,29,32");
+    if (c.threads != warp_kernel_threads())
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "warp kernel: threads must be " + std::to_string(warp_kernel_threads()));
+    if ((long long)32 * c.vec * 4 < h->ld)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "warp kernel: 32 * vec * 4 must cover the padded column (" +
+                      std::to_string(h->ld) + ")");
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32 || c.bisect_depth < 0 || c.bisect_depth > 30)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "bad ctas_per_sm or bisect_depth");
+    return MAM_OK;
+  }
   const int nvs[] = {1, 2, 3, 4, 5, 6, 8};
   if (std::find(std::begin(nvs), std::end(nvs), c.vec) == std::end(nvs))
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
@@ -191,12 +208,13 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
                 "threads * vec * 4 must cover the padded column (" +
                     std::to_string(h->ld) + ")");
   if (c.stages < 2 || c.stages > 4)
-    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "stages must be 2..4");
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "stages must be 0 (one warp per column) or 2..4");
   if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32)
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "ctas_per_sm must be 0..32");
   if (c.bisect_depth < 0 || c.bisect_depth > 30)
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "bisect_depth must be 0..30");
-  if (column_smem_bytes(h, c.stages) > 232448)
+  if (column_smem_bytes(h, c) > 232448)
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
                 "pipeline does not fit in shared memory; use fewer stages");
   return MAM_OK;
@@ -204,6 +222,21 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
 
 mam_kernel_config default_config(const mam_problem* h) {
   const int ld4 = h->ld / 4;
+  {
+    // Columns that fit one warp (32 lanes x vec float4 groups): one warp per
+    // column, the narrowest compiled width that covers the column.
+    const int need = (ld4 + 31) / 32;
+    for (int nv : {1, 2, 4, 7, 8, 13, 16, 24, 29, 32})
+      if (nv >= need) {
+        mam_kernel_config c{};
+        c.threads = warp_kernel_threads();
+        c.vec = nv;
+        c.stages = 0;
+        c.ctas_per_sm = 0;
+        c.bisect_depth = 4;
+        return c;
+      }
+  }
   const int nvs[] = {4, 5, 3, 6, 2, 8, 1};
   mam_kernel_config best{};
   double best_score = -1;
@@ -228,14 +261,19 @@ mam_kernel_config default_config(const mam_problem* h) {
 
 mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
   MAM_TRY(check_config(h, c));
-  const size_t smem = column_smem_bytes(h, c.stages);
+  const bool wk = c.stages == 0;
+  const size_t smem = wk ? warp_kernel_smem(c.vec) : column_smem_bytes(h, c);
   for (int dg = 0; dg < 2; ++dg)
-    MAM_CUDA(set_column_smem(c.vec, h->cost_dtype, dg != 0, smem), "cudaFuncSetAttribute");
+    MAM_CUDA(wk ? set_column_warp_smem(c.vec, h->cost_dtype, dg != 0, smem)
+                : set_column_smem(c.vec, h->cost_dtype, dg != 0, smem),
+             "cudaFuncSetAttribute");
   int occ = 0;
-  MAM_CUDA(column_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ),
+  MAM_CUDA(wk ? column_warp_occupancy(c.vec, h->cost_dtype, true, smem, &occ)
+              : column_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ),
            "occupancy");
   int occ2 = 0;
-  MAM_CUDA(column_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2),
+  MAM_CUDA(wk ? column_warp_occupancy(c.vec, h->cost_dtype, false, smem, &occ2)
+              : column_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2),
            "occupancy");
   occ = std::min(occ, occ2);
   if (occ < 1)
@@ -283,6 +321,7 @@ ColArgs col_args(const mam_problem* h) {
   a.lam = h->lam;
   a.nact = h->nact;
   a.col_meas = h->col_meas;
+  a.col_off = h->col_off_d;
   a.delta = h->delta;
   a.blk = h->blk;
   a.nblk = avg_blocks(h);
@@ -353,8 +392,11 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
     MAM_CUDA(cudaEventRecord(ev[0], h->stream), "cudaEventRecord");
   }
   const ColArgs ca = col_args(h);
-  MAM_CUDA(launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
-                         h->smem, h->stream, ca),
+  MAM_CUDA(h->cfg.stages == 0
+               ? launch_column_warp(h->cfg.vec, h->cost_dtype, diag, h->grid, h->smem,
+                                    h->stream, ca)
+               : launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
+                               h->smem, h->stream, ca),
            "column kernel launch");
   if (diag && h->nb > 1) {
     // Lower bound of every measure for the v^k the column step just used

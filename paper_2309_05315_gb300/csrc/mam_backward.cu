@@ -67,6 +67,13 @@ mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best) 
         }
     }
   }
+  for (int nv : {1, 2, 4, 7, 8, 13, 16, 24, 29, 32}) {
+    if (32 * nv * 4 < h->ld || 32 * nv * 4 > 4 * h->ld + 512) continue;
+    for (int cps : {0, 2, 3, 4}) {
+      mam_kernel_config c{warp_kernel_threads(), nv, 0, cps, start.bisect_depth};
+      if (check_config(h, c) == MAM_OK) cands.push_back(c);
+    }
+  }
   h->err.clear();
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

@@ -1,0 +1,252 @@
+// Device helpers shared by libmam's kernel translation units: PTX wrappers
+// (mbarrier, bulk-async copies, global timer), cost-type loads, CTA and warp
+// reductions, Remark 2 draws and t^k of Algorithm 1.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "mam_internal.h"
+
+namespace mam {
+namespace {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr int kMaxNewton = 64;  // bound on threshold-search passes / column
+
+// ------------------------------------------------------------------ PTX
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// One bulk copy global -> shared (sizes and addresses multiples of 16 B);
+// completion is reported as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src,
+                                          uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`, giving up after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar,
+                                                  uint32_t parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ cost types
+
+template <typename CT>
+struct CostIO;
+
+template <>
+struct CostIO<float> {
+  static __device__ __forceinline__ float4 load4(const float* base, int idx) {
+    return reinterpret_cast<const float4*>(base)[idx];
+  }
+};
+
+template <>
+struct CostIO<__nv_bfloat16> {
+  // bf16 -> fp32 is exact: the bf16 pattern is the top half of the fp32 one.
+  static __device__ __forceinline__ float4 load4(const __nv_bfloat16* base,
+                                                 int idx) {
+    const uint2 u = reinterpret_cast<const uint2*>(base)[idx];
+    return make_float4(__uint_as_float(u.x << 16),
+                       __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+  }
+};
+
+template <>
+struct CostIO<__half> {
+  static __device__ __forceinline__ float4 load4(const __half* base, int idx) {
+    const uint2 u = reinterpret_cast<const uint2*>(base)[idx];
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+};
+
+// ------------------------------------------------------------ reductions
+
+// CTA-wide reduction of (sum a, sum b, min-or-max c).  The xor butterfly
+// leaves identical values in every lane, and every thread then combines the
+// per-warp values in the same order, so all threads obtain bit-identical
+// results (the search below relies on that for uniform control flow).
+// `red` is double-buffered ([2][32]); alternating buffers makes one
+// __syncthreads per reduction sufficient.
+template <bool kMin>
+__device__ __forceinline__ void reduce3(float& a, float& b, float& c,
+                                        float4* red, int& rb, int lane,
+                                        int warp, int nw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    const float cc = __shfl_xor_sync(0xffffffffu, c, o);
+    c = kMin ? fminf(c, cc) : fmaxf(c, cc);
+  }
+  if (nw == 1) return;
+  if (lane == 0) red[rb * kRedSlots + warp] = make_float4(a, b, c, 0.f);
+  __syncthreads();
+  const float ident = kMin ? INFINITY : -INFINITY;
+  float4 r = lane < nw ? red[rb * kRedSlots + lane] : make_float4(0.f, 0.f, ident, 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+    r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+    const float cc = __shfl_xor_sync(0xffffffffu, r.z, o);
+    r.z = kMin ? fminf(r.z, cc) : fmaxf(r.z, cc);
+  }
+  a = r.x;
+  b = r.y;
+  c = r.z;
+  rb ^= 1;
+}
+
+template <int NV>
+struct MaxThreads {
+  static constexpr int value = NV == 1 ? 1024 : NV == 2 ? 768
+                               : NV <= 6 ? 512 : 384;
+};
+
+// ------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Index set of column step k (Remark 2): bundle i is drawn with probability
+// beta_i from u_k = (SplitMix64(seed + (k+1) * 0x9E3779B97F4A7C15) >> 11)
+// * 2^-53.  Deterministic MAM (nb <= 1) always uses index set 0.
+__device__ __forceinline__ int draw_index_set(const Draw& d, long long k) {
+  if (d.nb <= 1) return 0;
+  unsigned long long z = d.seed + (unsigned long long)k * 0x9E3779B97F4A7C15ull;
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const double u = double(z >> 11) * (1.0 / 9007199254740992.0);
+  int i = 0;
+  while (i < d.nb - 1 && !(u < d.cum[i])) ++i;
+  return i;
+}
+
+// t^k of Algorithm 1 from the averaging kernel's block sums of
+// sum_m ||p - p^(m)||^2 / S_m:  D = sqrt(sum), t = 1 if gamma = inf or
+// rho D <= gamma, else gamma / (rho D).  Every CTA of the column kernel
+// evaluates it with the same thread count and the same summation order, so
+// all of them obtain the same t.  Uses dred[0..31]; all threads must call.
+__device__ double t_from_blocks(const double* blk, int nblk, double rho,
+                                double gamma, double* dred, int tid, int nt) {
+  double acc = 0.0;
+  for (int i = tid; i < nblk; i += nt) acc += blk[4 * i];
+  acc = warp_sum_d(acc);
+  if ((tid & 31) == 0) dred[tid >> 5] = acc;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < (nt >> 5); ++w) tot += dred[w];
+  __syncthreads();
+  const double D = sqrt(tot);
+  if (isinf(gamma) || rho * D <= gamma) return 1.0;
+  return gamma / (rho * D);
+}
+
+// ------------------------------------------------------- packed FP32 pairs
+
+// Blackwell executes two FP32 lanes per instruction for add/sub/fma on
+// register pairs (PTX .f32x2).  Pairs are plain 64-bit registers here.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t pk(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float lo(f2_t r) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float hi(f2_t r) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+  return b;
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+  f2_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+  f2_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+  f2_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// (max(x.lo, 0), max(x.hi, 0)) and the number of positive lanes.
+__device__ __forceinline__ f2_t relu2(f2_t x, float& cnt) {
+  const float a = lo(x), b = hi(x);
+  cnt += (a > 0.f ? 1.f : 0.f) + (b > 0.f ? 1.f : 0.f);
+  return pk(fmaxf(a, 0.f), fmaxf(b, 0.f));
+}
+
+
+}  // namespace
+}  // namespace mam

@@ -142,7 +142,7 @@ Draw draw_args(const mam_problem* h);
 ColArgs col_args(const mam_problem* h);
 AvgArgs avg_args(const mam_problem* h, int reduce, int diag);
 int avg_blocks(const mam_problem* h);
-size_t column_smem_bytes(const mam_problem* h, int stages);
+size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c);
 void free_backward(mam_problem* h);
 mam_status reset_state(mam_problem* h);
 

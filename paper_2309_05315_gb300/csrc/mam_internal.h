@@ -36,6 +36,7 @@ struct ColArgs {
   float* lam;                // [T] last threshold lambda_s (NaN: none)
   float* nact;               // [T] active-set size at that threshold (0: none)
   const int* col_meas;       // [T] measure of each column
+  const long long* col_off;  // [Mtot+1] first column of each measure
   const double* delta;       // [Mtot][R] (p - p^(m)) / S_m
   const double* blk;         // [P][nblk][4] averaging block sums (dist^2 in [0])
   int nblk;
@@ -96,6 +97,15 @@ int column_max_threads(int nv);
 cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
                              size_t smem, int* blocks_per_sm);
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st);
+// One-warp-per-column variant (mam_warp_kernel.cu).
+bool warp_kernel_has(int nv);
+int warp_kernel_threads();
+size_t warp_kernel_smem(int nv);
+cudaError_t launch_column_warp(int nv, int cost_dtype, bool diag, int grid,
+                               size_t smem, cudaStream_t st, const ColArgs& a);
+cudaError_t set_column_warp_smem(int nv, int cost_dtype, bool diag, size_t smem);
+cudaError_t column_warp_occupancy(int nv, int cost_dtype, bool diag, size_t smem,
+                                  int* blocks_per_sm);
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const double* zeta, const double* gen_cost,
                               const int* col_meas, const double* alpha,

@@ -13,10 +13,7 @@
 // 4*ld (theta) and ld*sizeof(cost) bytes: each column is brought into shared
 // memory by two bulk-async copies (cp.async.bulk, completion on an mbarrier)
 // while the CTA works on the previous column.
-#include "mam_internal.h"
-
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include "mam_device.cuh"
 
 #include <cfloat>
 #include <cmath>
@@ -25,204 +22,13 @@
 namespace mam {
 namespace {
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
-constexpr int kMaxNewton = 64;  // bound on threshold-search passes / column
-
-// ------------------------------------------------------------------ PTX
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile(
-      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "r"(bytes)
-      : "memory");
-}
-
-// One bulk copy global -> shared (sizes and addresses multiples of 16 B);
-// completion is reported as transaction bytes on `bar`.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src,
-                                          uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for phase `parity` of `bar`, giving up after `limit_ns`.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar,
-                                                  uint32_t parity,
-                                                  unsigned long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-  return true;
-}
-
-// ------------------------------------------------------------ cost types
-
-template <typename CT>
-struct CostIO;
-
-template <>
-struct CostIO<float> {
-  static __device__ __forceinline__ float4 load4(const float* base, int idx) {
-    return reinterpret_cast<const float4*>(base)[idx];
-  }
-};
-
-template <>
-struct CostIO<__nv_bfloat16> {
-  // bf16 -> fp32 is exact: the bf16 pattern is the top half of the fp32 one.
-  static __device__ __forceinline__ float4 load4(const __nv_bfloat16* base,
-                                                 int idx) {
-    const uint2 u = reinterpret_cast<const uint2*>(base)[idx];
-    return make_float4(__uint_as_float(u.x << 16),
-                       __uint_as_float(u.x & 0xffff0000u),
-                       __uint_as_float(u.y << 16),
-                       __uint_as_float(u.y & 0xffff0000u));
-  }
-};
-
-template <>
-struct CostIO<__half> {
-  static __device__ __forceinline__ float4 load4(const __half* base, int idx) {
-    const uint2 u = reinterpret_cast<const uint2*>(base)[idx];
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-  }
-};
-
-// ------------------------------------------------------------ reductions
-
-// CTA-wide reduction of (sum a, sum b, min-or-max c).  The xor butterfly
-// leaves identical values in every lane, and every thread then combines the
-// per-warp values in the same order, so all threads obtain bit-identical
-// results (the search below relies on that for uniform control flow).
-// `red` is double-buffered ([2][32]); alternating buffers makes one
-// __syncthreads per reduction sufficient.
-template <bool kMin>
-__device__ __forceinline__ void reduce3(float& a, float& b, float& c,
-                                        float4* red, int& rb, int lane,
-                                        int warp, int nw) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    const float cc = __shfl_xor_sync(0xffffffffu, c, o);
-    c = kMin ? fminf(c, cc) : fmaxf(c, cc);
-  }
-  if (nw == 1) return;
-  if (lane == 0) red[rb * kRedSlots + warp] = make_float4(a, b, c, 0.f);
-  __syncthreads();
-  const float ident = kMin ? INFINITY : -INFINITY;
-  float4 r = lane < nw ? red[rb * kRedSlots + lane] : make_float4(0.f, 0.f, ident, 0.f);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
-    r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
-    const float cc = __shfl_xor_sync(0xffffffffu, r.z, o);
-    r.z = kMin ? fminf(r.z, cc) : fmaxf(r.z, cc);
-  }
-  a = r.x;
-  b = r.y;
-  c = r.z;
-  rb ^= 1;
-}
-
-template <int NV>
-struct MaxThreads {
-  static constexpr int value = NV == 1 ? 1024 : NV == 2 ? 768
-                               : NV <= 6 ? 512 : 384;
-};
-
-// ------------------------------------------------------- column kernel
-
-// ------------------------------------------------------------ helpers
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Index set of column step k (Remark 2): bundle i is drawn with probability
-// beta_i from u_k = (SplitMix64(seed + (k+1) * 0x9E3779B97F4A7C15) >> 11)
-// * 2^-53.  Deterministic MAM (nb <= 1) always uses index set 0.
-__device__ __forceinline__ int draw_index_set(const Draw& d, long long k) {
-  if (d.nb <= 1) return 0;
-  unsigned long long z = d.seed + (unsigned long long)k * 0x9E3779B97F4A7C15ull;
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  const double u = double(z >> 11) * (1.0 / 9007199254740992.0);
-  int i = 0;
-  while (i < d.nb - 1 && !(u < d.cum[i])) ++i;
-  return i;
-}
-
-// t^k of Algorithm 1 from the averaging kernel's block sums of
-// sum_m ||p - p^(m)||^2 / S_m:  D = sqrt(sum), t = 1 if gamma = inf or
-// rho D <= gamma, else gamma / (rho D).  Every CTA of the column kernel
-// evaluates it with the same thread count and the same summation order, so
-// all of them obtain the same t.  Uses dred[0..31]; all threads must call.
-__device__ double t_from_blocks(const double* blk, int nblk, double rho,
-                                double gamma, double* dred, int tid, int nt) {
-  double acc = 0.0;
-  for (int i = tid; i < nblk; i += nt) acc += blk[4 * i];
-  acc = warp_sum_d(acc);
-  if ((tid & 31) == 0) dred[tid >> 5] = acc;
-  __syncthreads();
-  double tot = 0.0;
-  for (int w = 0; w < (nt >> 5); ++w) tot += dred[w];
-  __syncthreads();
-  const double D = sqrt(tot);
-  if (isinf(gamma) || rho * D <= gamma) return 1.0;
-  return gamma / (rho * D);
-}
-
 // ------------------------------------------------------- column kernel
 
 // Step 2 of Algorithm 1 for one CTA's slice of the index set, one column at
 // a time.  Thread `tid` owns the float4 groups idx = v*nt + tid (v < NV) of
-// every column, i.e. rows r = 4*idx .. 4*idx+3; its shift d^(m)_r stays in
-// registers while consecutive columns belong to the same measure.
+// every column, i.e. rows r = 4*idx .. 4*idx+3, held as two FP32 pairs; its
+// shift d^(m)_r stays in registers while consecutive columns belong to the
+// same measure.
 //
 // Per column s of measure m (tau = q_s):
 //   w_r     = theta_rs + 2 d_r - c_rs / rho        (Alg. 1, w)
@@ -241,22 +47,15 @@ __device__ double t_from_blocks(const double* blk, int nblk, double rho,
 // lambda*, and from below it increases monotonically.  The active sets
 // {w > l} of two successive iterates are nested, so equal counts mean equal
 // sets, and then the later iterate is exactly lambda*.  The search starts
-// from the column's previous threshold (warm start); without one it brackets
-// lambda* in [max w - tau, max w), bisects bisect_depth times and continues
-// from the lower end.
+// from the column's previous threshold (warm start, usually one Newton step
+// and one confirming pass); without one it brackets lambda* in
+// [max w - tau, max w), bisects bisect_depth times and continues from the
+// lower end.
 //
-// Schedule of one column (warm start, the common case).  Pass 1 builds w and
-// evaluates (f, n) at the previous threshold l0.  The Newton iterate
-// l1 = l0 + (f - tau)/n satisfies l1 >= l0 - tau/n, so rows with
-// w <= l0 - tau/n can neither count in (f, n)(l1) nor be active at the
-// answer; pass 1 marks the float4 groups holding a row above
-// lc = l0 - 1.5 tau/n_prev (n_prev: the column's last active-set size) and
-// pass 2, at l1, visits only groups some lane of the warp marked (a
-// warp-uniform vote), computing the projection and theta' there.  When
-// l1 < lc (the guess n_prev was off) pass 2 visits everything.  Equal counts
-// in pass 1 and pass 2 confirm the active set and the registers are stored.
-// Two CTA-wide reductions per column; the shared-memory stage returns to
-// the copy engine right after the first.
+// Rows beyond R need no masks: the shared-memory tiles are threads*vec*4
+// long, their tails past the column hold theta = 0 and c = +inf (written
+// once per CTA), and the cost's padding rows R..ld-1 are +inf in memory, so
+// every such row has w = -inf and never enters the active set.
 template <int NV, typename CT, bool DIAG>
 __global__ void __launch_bounds__(MaxThreads<NV>::value)
     column_kernel(const ColArgs A) {
@@ -269,12 +68,13 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
   const int ld = A.ld;
   const int R = A.R;
   const int ld4 = ld >> 2;
+  const int tile = nt * NV * 4;  // elements per shared-memory stage
   const int stages = A.stages;
 
   float* th_s = reinterpret_cast<float*>(smem);
-  CT* c_s = reinterpret_cast<CT*>(smem + size_t(stages) * ld * sizeof(float));
+  CT* c_s = reinterpret_cast<CT*>(smem + size_t(stages) * tile * sizeof(float));
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      smem + size_t(stages) * ld * (sizeof(float) + sizeof(CT)));
+      smem + size_t(stages) * tile * (sizeof(float) + sizeof(CT)));
   float4* red = reinterpret_cast<float4*>(bar + 4);
   double* dred = reinterpret_cast<double*>(red + 2 * kRedSlots);
 
@@ -290,6 +90,12 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
   if (ncol > 0) {  // uniform over the CTA
     const uint32_t bytes_th = uint32_t(ld) * sizeof(float);
     const uint32_t bytes_c = uint32_t(ld) * sizeof(CT);
+    // Tails of every stage (never written by the copies).
+    for (int i = ld + tid; i < tile; i += nt)
+      for (int s = 0; s < stages; ++s) {
+        th_s[size_t(s) * tile + i] = 0.f;
+        c_s[size_t(s) * tile + i] = CT(INFINITY);
+      }
     if (tid == 0) {
       for (int s = 0; s < stages; ++s) mbar_init(&bar[s], 1);
       fence_mbar_init();
@@ -300,9 +106,9 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
       const int s = int(j % stages);
       const long long col = col0 + j;
       mbar_expect_tx(&bar[s], bytes_th + bytes_c);
-      bulk_load(th_s + size_t(s) * ld, A.theta + size_t(col) * ld, bytes_th,
+      bulk_load(th_s + size_t(s) * tile, A.theta + size_t(col) * ld, bytes_th,
                 &bar[s]);
-      bulk_load(c_s + size_t(s) * ld,
+      bulk_load(c_s + size_t(s) * tile,
                 static_cast<const CT*>(A.cost) + size_t(col) * ld, bytes_c,
                 &bar[s]);
     };
@@ -320,8 +126,10 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
       }
     };
 
-    float d[NV][4];
-    float rho_m = 0.f, irho_m = 0.f;
+    f2_t d2[NV][2];  // d for rows 4*idx + (0,1) and (2,3)
+    float rho_m = 0.f;
+    f2_t nirho2 = 0ull;
+    const f2_t two2 = pk(2.f, 2.f);
     int m_cur = -1, p_cur = -1;
     double t_cur = 1.0;
     unsigned long long* acc_m = nullptr;
@@ -332,18 +140,15 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
     int m_nx = A.col_meas[col0];
     float tau_nx = A.q[col0];
     float lam_nx = A.lam[col0];
-    float cnt_nx = A.nact[col0];
     for (long long j = 0; j < ncol; ++j) {
       const long long col = col0 + j;
       const int m = m_nx;
       const float tau = tau_nx;
       const float lam_prev = lam_nx;
-      const float cnt_prev = cnt_nx;
       if (j + 1 < ncol) {
         m_nx = A.col_meas[col + 1];
         tau_nx = A.q[col + 1];
         lam_nx = A.lam[col + 1];
-        cnt_nx = A.nact[col + 1];
       }
       if (m != m_cur) {  // first column of a measure in this slice
         m_cur = m;
@@ -355,195 +160,151 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
           if (tid == 0) A.t_used[pr] = t_cur;
         }
         rho_m = A.rho[m];
-        irho_m = A.inv_rho[m];
+        nirho2 = pk(-A.inv_rho[m], -A.inv_rho[m]);
         acc_m = A.acc + size_t(m) * R;
         const double* dl = A.delta + size_t(m) * R;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const int idx = v * nt + tid;
+          float dv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int r = 4 * idx + e;
-            d[v][e] = (idx < ld4 && r < R) ? float(t_cur * dl[r]) : 0.f;
+            dv[e] = r < R ? float(t_cur * dl[r]) : 0.f;
           }
+          d2[v][0] = pk(dv[0], dv[1]);
+          d2[v][1] = pk(dv[2], dv[3]);
         }
       }
       const int s = int(j % stages);
       const bool failed =
           !mbar_wait_bounded(&bar[s], uint32_t((j / stages) & 1), kWaitLimitNs);
-      const float* ths = th_s + size_t(s) * ld;
-      const CT* cs = c_s + size_t(s) * ld;
+      const float* ths = th_s + size_t(s) * tile;
+      const CT* cs = c_s + size_t(s) * tile;
       const bool pos = tau > 0.f;
       const bool warm = pos && (lam_prev == lam_prev);
       const float l0 = warm ? lam_prev : 0.f;
-      // Groups that can matter at the next Newton iterate (see above).
-      const float lc = (warm && cnt_prev >= 1.f) ? l0 - 1.5f * tau / cnt_prev : -INFINITY;
+      const f2_t l02 = pk(l0, l0);
 
-      // Pass 1: w, and (f, n) at l0 (max w as well when cold).
-      float w[NV][4];
-      bool mark[NV];
+      // Pass 1: w, and (f, n) at l0.
+      f2_t w2[NV][2];
       float lbmin = INFINITY;
-      float fv[NV], nv[NV];
-      float mx = -INFINITY;
+      f2_t fa = 0ull, fb = 0ull;  // two packed accumulators
+      float n = 0.f;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        fv[v] = 0.f;
-        nv[v] = 0.f;
-        mark[v] = false;
         const int idx = v * nt + tid;
-        if (idx < ld4) {
-          const float4 th = reinterpret_cast<const float4*>(ths)[idx];
-          const float4 c = CostIO<CT>::load4(cs, idx);
-          const float thv[4] = {th.x, th.y, th.z, th.w};
-          const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const bool ok = 4 * idx + e < R;
-            const float wv = ok ? (thv[e] + 2.f * d[v][e]) - cv[e] * irho_m : -INFINITY;
-            w[v][e] = wv;
-            const float x = wv - l0;
-            fv[v] += fmaxf(x, 0.f);
-            nv[v] += x > 0.f ? 1.f : 0.f;
-            mark[v] = mark[v] || wv > lc;
-            if (!warm) mx = fmaxf(mx, wv);
-            if (DIAG && ok) lbmin = fminf(lbmin, cv[e] - rho_m * d[v][e]);
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) w[v][e] = -INFINITY;
+        const float4 th = reinterpret_cast<const float4*>(ths)[idx];
+        const float4 c = CostIO<CT>::load4(cs, idx);
+        const f2_t c01 = pk(c.x, c.y), c23 = pk(c.z, c.w);
+        w2[v][0] = fma2(c01, nirho2, fma2(two2, d2[v][0], pk(th.x, th.y)));
+        w2[v][1] = fma2(c23, nirho2, fma2(two2, d2[v][1], pk(th.z, th.w)));
+        fa = add2(fa, relu2(sub2(w2[v][0], l02), n));
+        fb = add2(fb, relu2(sub2(w2[v][1], l02), n));
+        if (DIAG) {
+          lbmin = fminf(lbmin, fminf(fminf(c.x - rho_m * lo(d2[v][0]), c.y - rho_m * hi(d2[v][0])),
+                                     fminf(c.z - rho_m * lo(d2[v][1]), c.w - rho_m * hi(d2[v][1]))));
         }
       }
-      float f = 0.f, n = 0.f;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        f += fv[v];
-        n += nv[v];
+      // The failure flag rides in the first reduction (f < 0 marks it).
+      {
+        const f2_t fs = add2(fa, fb);
+        float f = lo(fs) + hi(fs);
+        if (failed) f = -INFINITY;
+        float z = 0.f;
+        reduce3<false>(f, n, z, red, rb, lane, warp, nw);
+        if (!DIAG) refill(j);
+        any_fail = !(f >= 0.f);
+        fa = pk(f, 0.f);  // keep f (lo) for the search below
       }
-      // The failure flag rides in the first reduction (uniform afterwards).
-      float flag = failed ? 1.f : 0.f;
-      if (warm) {
-        reduce3<false>(f, n, flag, red, rb, lane, warp, nw);
-      } else {
-        reduce3<false>(flag, n, mx, red, rb, lane, warp, nw);
-      }
-      if (!DIAG) refill(j);
       int np = 1;
-      any_fail = flag > 0.f;
-
-      float o[NV][4];
       float lam_fin = INFINITY;
-      float n_fin = 0.f;
-      bool have_o = false;
-      bool sparse = false;  // o holds -d in unvisited groups
       if (pos) {
+        float f = lo(fa);
         float nprev = -1.f;
         bool bracket = !warm;
         float lam = l0;
         if (warm) {
-          if (n == 0.f) {
-            bracket = true;  // warm start at or above max w: need max w
-          } else {
+          if (n == 0.f) bracket = true;  // warm start at or above max w
+          else {
             lam = l0 + (f - tau) / n;
             nprev = n;
-            sparse = lam >= lc;
           }
         }
         for (int it = 0; it < kMaxNewton; ++it) {
           if (bracket) {  // lambda* lies in [max w - tau, max w)
-            if (warm) {   // max w was not reduced in pass 1
-              float z0 = 0.f, z1 = 0.f;
-              mx = -INFINITY;
+            float mx = -INFINITY, z0 = 0.f, z1 = 0.f;
 #pragma unroll
-              for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) mx = fmaxf(mx, w[v][e]);
-              reduce3<false>(z0, z1, mx, red, rb, lane, warp, nw);
-              ++np;
-            }
-            float lo = mx - tau, hi = mx;
+            for (int v = 0; v < NV; ++v)
+              mx = fmaxf(mx, fmaxf(fmaxf(lo(w2[v][0]), hi(w2[v][0])),
+                                   fmaxf(lo(w2[v][1]), hi(w2[v][1]))));
+            reduce3<false>(z0, z1, mx, red, rb, lane, warp, nw);
+            ++np;
+            float lo_b = mx - tau, hi_b = mx;
             for (int b = 0; b < A.bisect_depth; ++b) {
-              const float mid = 0.5f * (lo + hi);
-              float fb = 0.f, z = 0.f, y = 0.f;
+              const float mid = 0.5f * (lo_b + hi_b);
+              const f2_t mid2 = pk(mid, mid);
+              f2_t ga = 0ull;
+              float cnt = 0.f, zz = 0.f;
 #pragma unroll
-              for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) fb += fmaxf(w[v][e] - mid, 0.f);
-              reduce3<false>(fb, z, y, red, rb, lane, warp, nw);
+              for (int v = 0; v < NV; ++v) {
+                ga = add2(ga, relu2(sub2(w2[v][0], mid2), cnt));
+                ga = add2(ga, relu2(sub2(w2[v][1], mid2), cnt));
+              }
+              float fm = lo(ga) + hi(ga);
+              reduce3<false>(fm, cnt, zz, red, rb, lane, warp, nw);
               ++np;
-              if (fb >= tau) lo = mid; else hi = mid;
+              if (fm >= tau) lo_b = mid; else hi_b = mid;
             }
-            lam = lo;
+            lam = lo_b;
             nprev = -1.f;
             bracket = false;
-            sparse = false;
           }
-          // (f, n) at lam, with the projection computed on the way.
+          // (f, n) at lam.
+          const f2_t lam2 = pk(lam, lam);
+          f2_t ga = 0ull, gb = 0ull;
+          float cnt = 0.f;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            fv[v] = 0.f;
-            nv[v] = 0.f;
-            const bool visit = !sparse || __any_sync(0xffffffffu, mark[v]);
-            if (visit) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float x = w[v][e] - lam;
-                const float pv = fmaxf(x, 0.f);
-                fv[v] += pv;
-                nv[v] += x > 0.f ? 1.f : 0.f;
-                o[v][e] = pv - d[v][e];
-              }
-            } else {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) o[v][e] = -d[v][e];
-            }
+            ga = add2(ga, relu2(sub2(w2[v][0], lam2), cnt));
+            gb = add2(gb, relu2(sub2(w2[v][1], lam2), cnt));
           }
-          f = 0.f;
-          n = 0.f;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            f += fv[v];
-            n += nv[v];
-          }
+          const f2_t gs = add2(ga, gb);
+          f = lo(gs) + hi(gs);
           float z = 0.f;
-          reduce3<false>(f, n, z, red, rb, lane, warp, nw);
+          reduce3<false>(f, cnt, z, red, rb, lane, warp, nw);
           ++np;
-          if (n == nprev) {  // same active set twice: lam is the threshold
-            have_o = true;
+          if (cnt == nprev) {  // same active set twice: lam is the threshold
             lam_fin = lam;
-            n_fin = n;
             break;
           }
-          sparse = false;  // later passes visit every group
-          if (n == 0.f) {  // not expected from below; restart from the bracket
+          if (cnt == 0.f) {  // not expected from below; restart from the bracket
             bracket = true;
             continue;
           }
-          nprev = n;
-          lam = lam + (f - tau) / n;
-        }
-        if (!have_o) {  // pass budget exhausted (not expected): use the last lam
-          lam_fin = lam;
-          n_fin = nprev;
+          nprev = cnt;
+          lam = lam + (f - tau) / cnt;
+          lam_fin = lam;  // used if the pass budget runs out (not expected)
         }
       }
 
       // Commit: theta' = pihat - d, Step 3 row sums (+ diagnostics).
+      const f2_t lf2 = pk(lam_fin, lam_fin);
       float wc = 0.f, res = 0.f;
       float4* gth = reinterpret_cast<float4*>(A.theta + size_t(col) * ld);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int idx = v * nt + tid;
-        float pv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) pv[e] = fmaxf(w[v][e] - lam_fin, 0.f);
-        if (!have_o) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) o[v][e] = pv[e] - d[v][e];
-        }
+        float dummy = 0.f;
+        const f2_t p01 = relu2(sub2(w2[v][0], lf2), dummy);
+        const f2_t p23 = relu2(sub2(w2[v][1], lf2), dummy);
+        const f2_t o01 = sub2(p01, d2[v][0]);
+        const f2_t o23 = sub2(p23, d2[v][1]);
+        const float pv[4] = {lo(p01), hi(p01), lo(p23), hi(p23)};
         // pihat is sparse: convert and add only where some lane of the warp
         // has an active row in this group.
-        const bool act = pv[0] > 0.f || pv[1] > 0.f || pv[2] > 0.f || pv[3] > 0.f;
-        if (__any_sync(0xffffffffu, act) && act && idx < ld4) {
+        const bool act = fmaxf(fmaxf(pv[0], pv[1]), fmaxf(pv[2], pv[3])) > 0.f;
+        if (__any_sync(0xffffffffu, act) && act) {
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             if (pv[e] > 0.f)
@@ -551,21 +312,21 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
                         (unsigned long long)__float2ll_rn(pv[e] * fx));
         }
         if (idx < ld4) {
+          const float4 ov = make_float4(lo(o01), hi(o01), lo(o23), hi(o23));
           if (DIAG) {
             const float4 th = reinterpret_cast<const float4*>(ths)[idx];
             const float4 c = CostIO<CT>::load4(cs, idx);
             const float thv[4] = {th.x, th.y, th.z, th.w};
             const float cv[4] = {c.x, c.y, c.z, c.w};
+            const float ovv[4] = {ov.x, ov.y, ov.z, ov.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              if (4 * idx + e < R) {
-                wc += cv[e] * pv[e];
-                const float dd = o[v][e] - thv[e];
-                res += dd * dd;
-              }
+              if (pv[e] > 0.f) wc += cv[e] * pv[e];
+              const float dd = ovv[e] - thv[e];
+              res += dd * dd;
             }
           }
-          gth[idx] = make_float4(o[v][0], o[v][1], o[v][2], o[v][3]);
+          gth[idx] = ov;
         }
       }
       if (DIAG) {
@@ -577,10 +338,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         }
         refill(j);  // the reduction's barrier ended every read of stage s
       }
-      if (tid == 0) {
-        A.lam[col] = lam_fin;
-        A.nact[col] = n_fin;
-      }
+      if (tid == 0) A.lam[col] = lam_fin;
       my_passes += np;
       if (any_fail) break;  // uniform: the flag went through a reduction
     }
@@ -710,7 +468,7 @@ __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
 
 // c_rs = alpha_m * ||xi_r - zeta_s||^2 (eq. HugeLP) or alpha_m * C_rs,
 // computed in FP64 without contraction, rounded to FP32, then to the storage
-// type (round to nearest even).  Padding rows get 0.  zeta and gen hold the
+// type (round to nearest even).  Padding rows R..ld-1 get +inf.  zeta and gen hold the
 // columns col0 .. col0+ncols-1 only.
 template <typename CT>
 __device__ __forceinline__ CT to_cost(float x);
@@ -737,7 +495,7 @@ __global__ void build_cost_kernel(CT* cost, const double* xi,
     const long long jc = i / ld;
     const int r = int(i - jc * ld);
     const long long col = col0 + jc;
-    double c = 0.0;
+    double c = INFINITY;  // padding rows: w = -inf, never active
     if (r < R) {
       const double al = alpha[col_meas[col]];
       if (gen) {
