@@ -221,6 +221,32 @@ mam_status mam_profile_enable(mam_problem* h, int32_t enable);
 mam_status mam_profile_read(mam_problem* h, double* column_ms, double* average_ms,
                             int64_t* launches);
 
+/* Column update without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * code whose device memory is owned by another framework's pool (a raw
+ * allocation bypasses that pool and may fail once it has reserved the GPU)
+ * or latency-critical loops that cannot afford cudaMalloc's implicit
+ * synchronisation.  On one measure's plan it computes, for every column s,
+ * w = theta_s + 2 d - c_s / rho, pihat_s = Proj_{Delta_R(q_s)}(w) and
+ * theta_s <- pihat_s - d (in place), and writes rowsum_out[r] =
+ * sum_s theta_rs (FP64).  All pointers are device pointers the caller owns:
+ * theta and cost [S][ld] FP32 (column-contiguous, ld >= R), q [S], d [R],
+ * rowsum_out [R].  mass_bound must be >= sum_s q_s (it fixes the scale of
+ * the integer accumulator).  Work is enqueued on `stream` (NULL = default
+ * stream); the call does not synchronise.
+ * Scratch: a file-scope device array of 12288 64-bit integers (96 KB) that
+ * every GPU loading the library keeps until exit; R > 12288 is rejected with
+ * MAM_ERR_INVALID_ARG.  The array is cleared at the start of every call, and
+ * all calls on a device share it, so calls whose work overlaps on the GPU
+ * (different streams, concurrently) race and give wrong row sums.  The first
+ * call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Errors go to
+ * mam_last_error(NULL). */
+mam_status mam_column_update_noalloc(float* theta, const float* cost, const float* q,
+                                     const float* d, int32_t R, int32_t ld, int32_t S,
+                                     double rho, double mass_bound, double* rowsum_out,
+                                     void* stream);
+
 /* Last error message of h, or the thread-local one when h is NULL. */
 const char* mam_last_error(const mam_problem* h);
 

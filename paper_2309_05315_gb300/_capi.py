@@ -87,6 +87,9 @@ _SIGS = {
     "mam_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "mam_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
+    "mam_column_update_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                            C.c_double, C.c_void_p, C.c_void_p]),
     "mam_last_error": (C.c_char_p, [C.c_void_p]),
     "mam_destroy": (None, [C.c_void_p]),
 }
