@@ -193,17 +193,22 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every);
 mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
                         double* grad_zeta, double* grad_xi);
 
-/* Kernel configuration: threads per column (multiple of 32, <= 1024),
- * float4 vectors per thread (1..8), pipeline stages (2..4), CTAs per SM
- * (0 = occupancy maximum), and the bisection depth used on a cold start
- * (0..30).  Returns MAM_ERR_INVALID_ARG for a configuration that cannot
- * cover R. */
+/* Kernel configuration of the column step.
+ * kind 0: one CTA per column.  threads (multiple of 32, <= 1024) x vec
+ *   (1..6 or 8) float4 groups cover the column; stages (2..4) is the depth
+ *   of the bulk-copy pipeline.  Any R up to 12288.
+ * kind 1: one warp per column.  vec (1,2,4,7,8,13,16,24,29,32) float4 groups
+ *   per lane cover the column (R up to 4096); stages (>= threads/32) is the
+ *   number of shared-memory ring slots; threads/32 warps per CTA.
+ * ctas_per_sm: 0 = occupancy maximum.  bisect_depth (0..30): bisection steps
+ * on a cold start.  Invalid combinations return MAM_ERR_INVALID_ARG. */
 typedef struct {
   int32_t threads;
   int32_t vec;
   int32_t stages;
   int32_t ctas_per_sm;
   int32_t bisect_depth;
+  int32_t kind;
 } mam_kernel_config;
 mam_status mam_get_config(const mam_problem* h, mam_kernel_config* cfg);
 mam_status mam_set_config(mam_problem* h, const mam_kernel_config* cfg);

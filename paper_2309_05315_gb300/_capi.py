@@ -48,7 +48,8 @@ class MamObjective(C.Structure):
 
 class MamKernelConfig(C.Structure):
     _fields_ = [("threads", C.c_int32), ("vec", C.c_int32), ("stages", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("bisect_depth", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("bisect_depth", C.c_int32),
+                ("kind", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

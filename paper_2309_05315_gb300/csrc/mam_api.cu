@@ -180,21 +180,30 @@ size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c) {
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
-  if (c.stages == 0) {  // one warp per column
-    if (!warp_kernel_has(c.vec))
+  if (c.kind == 1) {  // one warp per column, shared-memory ring
+    if (!ring_kernel_has(c.vec))
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
-                  "warp kernel: vec must be one of 1,2,4,7,8,13,16,24,29,32");
-    if (c.threads != warp_kernel_threads())
+                  "kind 1: vec must be one of 1,2,4,7,8,13,16,24,29,32");
+    if (c.threads < 32 || c.threads % 32 || c.threads > ring_kernel_max_threads(c.vec))
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
-                  "warp kernel: threads must be " + std::to_string(warp_kernel_threads()));
+                  "kind 1: threads must be a multiple of 32 up to " +
+                      std::to_string(ring_kernel_max_threads(c.vec)));
     if ((long long)32 * c.vec * 4 < h->ld)
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
-                  "warp kernel: 32 * vec * 4 must cover the padded column (" +
+                  "kind 1: 32 * vec * 4 must cover the padded column (" +
                       std::to_string(h->ld) + ")");
+    if (c.stages < c.threads / 32 || c.stages > 64)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "kind 1: stages (ring slots) must be >= warps per CTA and <= 64");
+    if (ring_kernel_smem(c.vec, c.stages, int(cost_elem_size(h->cost_dtype))) > 232448)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "kind 1: ring does not fit in shared memory; use fewer slots");
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32 || c.bisect_depth < 0 || c.bisect_depth > 30)
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "bad ctas_per_sm or bisect_depth");
     return MAM_OK;
   }
+  if (c.kind != 0)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "kind must be 0 or 1");
   const int nvs[] = {1, 2, 3, 4, 5, 6, 8};
   if (std::find(std::begin(nvs), std::end(nvs), c.vec) == std::end(nvs))
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
@@ -220,21 +229,33 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
   return MAM_OK;
 }
 
+// The one-CTA-per-column kernel measured faster than the warp-per-column
+// ring on the R = 3600 workload (62 us vs 81 us per column step); the ring
+// stays available through mam_set_config / mam_autotune.
+constexpr bool kDefaultRing = false;
+
 mam_kernel_config default_config(const mam_problem* h) {
   const int ld4 = h->ld / 4;
-  {
+  if (kDefaultRing) {
     // Columns that fit one warp (32 lanes x vec float4 groups): one warp per
-    // column, the narrowest compiled width that covers the column.
+    // column, the narrowest compiled width that covers the column, as many
+    // ring slots as fit one CTA per SM, one warp per slot.
     const int need = (ld4 + 31) / 32;
     for (int nv : {1, 2, 4, 7, 8, 13, 16, 24, 29, 32})
       if (nv >= need) {
         mam_kernel_config c{};
-        c.threads = warp_kernel_threads();
+        c.kind = 1;
         c.vec = nv;
-        c.stages = 0;
-        c.ctas_per_sm = 0;
+        const size_t slot = ring_kernel_smem(nv, 1, int(cost_elem_size(h->cost_dtype)));
+        int K = int((232448 - 64) / slot);
+        K = std::min(K, 32);
+        const int W = std::min(K, ring_kernel_max_threads(nv) / 32);
+        c.stages = K;
+        c.threads = 32 * W;
+        c.ctas_per_sm = 1;
         c.bisect_depth = 4;
-        return c;
+        if (W >= 1) return c;
+        break;
       }
   }
   const int nvs[] = {4, 5, 3, 6, 2, 8, 1};
@@ -256,23 +277,25 @@ mam_kernel_config default_config(const mam_problem* h) {
   best.stages = 2;
   best.ctas_per_sm = 0;
   best.bisect_depth = 4;
+  best.kind = 0;
   return best;
 }
 
 mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
   MAM_TRY(check_config(h, c));
-  const bool wk = c.stages == 0;
-  const size_t smem = wk ? warp_kernel_smem(c.vec) : column_smem_bytes(h, c);
+  const bool wk = c.kind == 1;
+  const size_t smem = wk ? ring_kernel_smem(c.vec, c.stages, int(cost_elem_size(h->cost_dtype)))
+                         : column_smem_bytes(h, c);
   for (int dg = 0; dg < 2; ++dg)
-    MAM_CUDA(wk ? set_column_warp_smem(c.vec, h->cost_dtype, dg != 0, smem)
+    MAM_CUDA(wk ? set_column_ring_smem(c.vec, h->cost_dtype, dg != 0, smem)
                 : set_column_smem(c.vec, h->cost_dtype, dg != 0, smem),
              "cudaFuncSetAttribute");
   int occ = 0;
-  MAM_CUDA(wk ? column_warp_occupancy(c.vec, h->cost_dtype, true, smem, &occ)
+  MAM_CUDA(wk ? column_ring_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ)
               : column_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ),
            "occupancy");
   int occ2 = 0;
-  MAM_CUDA(wk ? column_warp_occupancy(c.vec, h->cost_dtype, false, smem, &occ2)
+  MAM_CUDA(wk ? column_ring_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2)
               : column_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2),
            "occupancy");
   occ = std::min(occ, occ2);
@@ -323,6 +346,7 @@ ColArgs col_args(const mam_problem* h) {
   a.col_meas = h->col_meas;
   a.col_off = h->col_off_d;
   a.delta = h->delta;
+  a.delta32 = h->delta32;
   a.blk = h->blk;
   a.nblk = avg_blocks(h);
   a.rho_p = h->rho_d;
@@ -368,6 +392,8 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   a.pm = h->pm;
   a.p = h->p;
   a.delta = h->delta;
+  a.delta32 = h->delta32;
+  a.ld = h->ld;
   a.phat = h->phat;
   a.blk = h->blk;
   return a;
@@ -392,9 +418,9 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
     MAM_CUDA(cudaEventRecord(ev[0], h->stream), "cudaEventRecord");
   }
   const ColArgs ca = col_args(h);
-  MAM_CUDA(h->cfg.stages == 0
-               ? launch_column_warp(h->cfg.vec, h->cost_dtype, diag, h->grid, h->smem,
-                                    h->stream, ca)
+  MAM_CUDA(h->cfg.kind == 1
+               ? launch_column_ring(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
+                                    h->smem, h->stream, ca)
                : launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
                                h->smem, h->stream, ca),
            "column kernel launch");
@@ -484,6 +510,7 @@ mam_status reset_state(mam_problem* h) {
   MAM_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * h->P * h->R, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->acc, 0, sizeof(unsigned long long) * MR, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->phat, 0, sizeof(double) * MR, h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->delta32, 0, sizeof(float) * size_t(h->Mtot) * h->ld, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->diag_wc, 0, sizeof(float) * h->T, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->diag_lb, 0, sizeof(float) * h->T, h->stream), "memset");
   MAM_CUDA(cudaMemsetAsync(h->diag_res, 0, sizeof(float) * h->T, h->stream), "memset");
@@ -666,6 +693,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->pm, MR, "marginals");
   ALLOC(h->delta, MR, "shifts");
   ALLOC(h->acc, MR, "row-sum accumulators");
+  ALLOC(h->delta32, size_t(h->Mtot) * h->ld, "shifts (fp32)");
   ALLOC(h->phat, MR, "pi-hat marginals");
   ALLOC(h->p, size_t(h->P) * h->R, "barycenters");
   ALLOC(h->t_used, size_t(h->P), "t");
@@ -1010,6 +1038,7 @@ std::vector<Piece> state_pieces(mam_problem* h) {
           {h->pm, sizeof(double) * MR},
           {h->p, sizeof(double) * size_t(h->P) * h->R},
           {h->delta, sizeof(double) * MR},
+          {h->delta32, sizeof(float) * size_t(h->Mtot) * h->ld},
           {h->phat, sizeof(double) * MR},
           {h->t_used, sizeof(double) * h->P},
           {h->blk, sizeof(double) * 4 * size_t(h->P) * avg_blocks(h)},

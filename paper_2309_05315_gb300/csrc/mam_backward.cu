@@ -62,17 +62,20 @@ mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best) 
       if (t > column_max_threads(nv)) continue;
       for (int stg = 2; stg <= 3; ++stg)
         for (int cps : {0, 1, 2}) {
-          mam_kernel_config c{t, nv, stg, cps, start.bisect_depth};
+          mam_kernel_config c{t, nv, stg, cps, start.bisect_depth, 0};
           if (check_config(h, c) == MAM_OK) cands.push_back(c);
         }
     }
   }
   for (int nv : {1, 2, 4, 7, 8, 13, 16, 24, 29, 32}) {
-    if (32 * nv * 4 < h->ld || 32 * nv * 4 > 4 * h->ld + 512) continue;
-    for (int cps : {0, 2, 3, 4}) {
-      mam_kernel_config c{warp_kernel_threads(), nv, 0, cps, start.bisect_depth};
-      if (check_config(h, c) == MAM_OK) cands.push_back(c);
-    }
+    if (32 * nv * 4 < h->ld || 32 * nv * 4 > 2 * h->ld + 512) continue;
+    for (int K : {2, 4, 7, 8, 12, 16, 24, 32})
+      for (int W : {2, 4, 7, 8, 12, 16})
+        for (int cps : {1, 2}) {
+          if (W > K) continue;
+          mam_kernel_config c{32 * W, nv, K, cps, start.bisect_depth, 1};
+          if (check_config(h, c) == MAM_OK) cands.push_back(c);
+        }
   }
   h->err.clear();
   cudaEvent_t e0, e1;

@@ -82,6 +82,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar,
   return true;
 }
 
+// Programmatic dependent launch: wait until the preceding kernel in the
+// stream has finished and its writes are visible / let the next kernel start
+// its prologue.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------ cost types
 
 template <typename CT>
@@ -247,6 +255,23 @@ __device__ __forceinline__ f2_t relu2(f2_t x, float& cnt) {
   return pk(fmaxf(a, 0.f), fmaxf(b, 0.f));
 }
 
+
+// Launch `kernel` with programmatic stream serialization (see pdl_wait).
+template <typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 }  // namespace
 }  // namespace mam

@@ -59,6 +59,7 @@ struct mam_problem {
   float* lam = nullptr;
   double* pm = nullptr;
   double* delta = nullptr;
+  float* delta32 = nullptr;
   double* phat = nullptr;
   double* p = nullptr;
   double* t_used = nullptr;

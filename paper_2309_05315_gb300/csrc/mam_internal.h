@@ -38,6 +38,7 @@ struct ColArgs {
   const int* col_meas;       // [T] measure of each column
   const long long* col_off;  // [Mtot+1] first column of each measure
   const double* delta;       // [Mtot][R] (p - p^(m)) / S_m
+  const float* delta32;      // [Mtot][ld] the same in FP32, zero past R
   const double* blk;         // [P][nblk][4] averaging block sums (dist^2 in [0])
   int nblk;
   const double* rho_p;       // [P]
@@ -82,6 +83,8 @@ struct AvgArgs {
   double* pm;                // [Mtot][R]
   double* p;                 // [P][R]
   double* delta;             // [Mtot][R]
+  float* delta32;            // [Mtot][ld] FP32 copy the column kernels read
+  int ld;
   double* phat;              // [Mtot][R] row sums of pi-hat (DIAG)
   double* blk;               // [P][nblk][4] block sums: dist^2, dist_hat^2, |dp|^2
 };
@@ -97,15 +100,15 @@ int column_max_threads(int nv);
 cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
                              size_t smem, int* blocks_per_sm);
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st);
-// One-warp-per-column variant (mam_warp_kernel.cu).
-bool warp_kernel_has(int nv);
-int warp_kernel_threads();
-size_t warp_kernel_smem(int nv);
-cudaError_t launch_column_warp(int nv, int cost_dtype, bool diag, int grid,
+// One warp per column with a shared-memory ring (mam_warp_kernel.cu).
+bool ring_kernel_has(int nv);
+int ring_kernel_max_threads(int nv);
+size_t ring_kernel_smem(int nv, int slots, int cost_bytes);
+cudaError_t launch_column_ring(int nv, int cost_dtype, bool diag, int grid, int threads,
                                size_t smem, cudaStream_t st, const ColArgs& a);
-cudaError_t set_column_warp_smem(int nv, int cost_dtype, bool diag, size_t smem);
-cudaError_t column_warp_occupancy(int nv, int cost_dtype, bool diag, size_t smem,
-                                  int* blocks_per_sm);
+cudaError_t set_column_ring_smem(int nv, int cost_dtype, bool diag, size_t smem);
+cudaError_t column_ring_occupancy(int nv, int cost_dtype, bool diag, int threads,
+                                  size_t smem, int* blocks_per_sm);
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const double* zeta, const double* gen_cost,
                               const int* col_meas, const double* alpha,

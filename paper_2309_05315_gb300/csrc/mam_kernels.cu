@@ -137,6 +137,10 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
     int rb = 0;
 
     // Per-column scalars are loaded one column ahead.
+    // Everything above only touched this kernel's own inputs (plans and costs
+    // written by the previous column step); from here on the averaging
+    // kernel's outputs (shifts, block sums, cleared accumulators) are used.
+    pdl_wait();
     int m_nx = A.col_meas[col0];
     float tau_nx = A.q[col0];
     float lam_nx = A.lam[col0];
@@ -162,7 +166,8 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         rho_m = A.rho[m];
         nirho2 = pk(-A.inv_rho[m], -A.inv_rho[m]);
         acc_m = A.acc + size_t(m) * R;
-        const double* dl = A.delta + size_t(m) * R;
+        const float* dl = A.delta32 + size_t(m) * ld;
+        const float tf = float(t_cur);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const int idx = v * nt + tid;
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int r = 4 * idx + e;
-            dv[e] = r < R ? float(t_cur * dl[r]) : 0.f;
+            dv[e] = r < R ? __fmul_rn(tf, dl[r]) : 0.f;
           }
           d2[v][0] = pk(dv[0], dv[1]);
           d2[v][1] = pk(dv[2], dv[3]);
@@ -352,6 +357,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
   }
   if (tid == 0) {
     atomicAdd(A.passes, my_passes);
+    pdl_wait();  // (CTAs with no columns reach this point directly)
     // The last CTA to finish advances the iteration counter (every CTA has
     // read it by then).
     __threadfence();
@@ -381,6 +387,8 @@ __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
   __shared__ double sp[kAvgSlices][kAvgRows];
   __shared__ double sq[kAvgSlices][kAvgRows];
   __shared__ double sr[kAvgRows * kAvgSlices / 32][3];
+  pdl_wait();         // the column step's row sums and t are complete
+  pdl_launch_next();  // the next column step may start copying its columns
   const int pr = blockIdx.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = blockIdx.x * kAvgRows + tx;
@@ -398,7 +406,8 @@ __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
         const double sum_pihat = double((long long)A.acc[o]) * A.fx_inv_scale;
         A.acc[o] = 0ull;
         // the column kernel subtracted d = float(t delta) from every entry
-        const double d_used = double(float(t_old * A.delta[o]));
+        const double d_used =
+            double(__fmul_rn(float(t_old), A.delta32[size_t(m) * A.ld + r]));
         if (A.diag) A.phat[o] = sum_pihat;
         pmv = sum_pihat - A.Sd[m] * d_used;
         A.pm[o] = pmv;
@@ -427,6 +436,7 @@ __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
       const double dfs = df * is;
       e += df * dfs;
       A.delta[o] = dfs;
+      A.delta32[size_t(m) * A.ld + r] = float(dfs);
       if (A.diag) {
         const double dh = ph - A.phat[o];
         eh += dh * dh * is;
@@ -625,8 +635,7 @@ __global__ void __launch_bounds__(256) lb_kernel(
 template <int NV, typename CT, bool DIAG>
 cudaError_t launch_col_t(int grid, int threads, size_t smem, cudaStream_t st,
                          const ColArgs& a) {
-  column_kernel<NV, CT, DIAG><<<grid, threads, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(column_kernel<NV, CT, DIAG>, dim3(grid), dim3(threads), smem, st, a);
 }
 
 template <int NV, typename CT, bool DIAG>
@@ -713,8 +722,7 @@ cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
 }
 
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st) {
-  average_kernel<<<dim3(nblk, a.P), dim3(kAvgRows, kAvgSlices), 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(average_kernel, dim3(nblk, a.P), dim3(kAvgRows, kAvgSlices), 0, st, a);
 }
 
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,

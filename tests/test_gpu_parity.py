@@ -158,18 +158,28 @@ def test_randomized_bundles(Mam):
 
 
 @pytest.mark.parametrize("cfg", [
-    dict(threads=32, vec=2, stages=2),
-    dict(threads=64, vec=1, stages=3),
-    dict(threads=32, vec=8, stages=4, ctas_per_sm=1),
-    dict(threads=96, vec=1, stages=2, ctas_per_sm=2),
+    dict(kind=0, threads=32, vec=2, stages=2),
+    dict(kind=0, threads=64, vec=1, stages=3),
+    dict(kind=0, threads=32, vec=8, stages=4, ctas_per_sm=1),
+    dict(kind=0, threads=96, vec=1, stages=2, ctas_per_sm=2),
+    dict(kind=1, threads=32, vec=2, stages=2, ctas_per_sm=4),
+    dict(kind=1, threads=128, vec=2, stages=8, ctas_per_sm=1),
+    dict(kind=1, threads=224, vec=4, stages=7, ctas_per_sm=1),
+    dict(kind=1, threads=64, vec=8, stages=3, ctas_per_sm=2),
 ])
 def test_kernel_configurations(Mam, cfg):
     compare_trajectory(Mam, config1(), 20, config=cfg)
 
 
 def test_cold_start_bisection_depths(Mam):
-    for depth in (0, 12, 30):
-        compare_trajectory(Mam, config1(), 5, config=dict(bisect_depth=depth))
+    for kind, extra in ((1, {}), (0, dict(threads=64, vec=1, stages=2))):
+        for depth in (0, 12, 30):
+            compare_trajectory(Mam, config1(), 5, config=dict(kind=kind, bisect_depth=depth, **extra))
+
+
+def test_config2_cta_kernel_iterates(Mam):
+    """The one-CTA-per-column kernel on the R = 3600 workload."""
+    compare_trajectory(Mam, config2(), 3, config=dict(kind=0, threads=160, vec=6, stages=2))
 
 
 def test_diagnostics_match_oracle(Mam):
