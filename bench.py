@@ -91,7 +91,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mam_kernels.cu", "mam_internal.h"):
+    for f in ("mam_kernels.cu", "mam_device.cuh", "mam_internal.h"):
         with open(os.path.join(ROOT, "paper_2309_05315_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

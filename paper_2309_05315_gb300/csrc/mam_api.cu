@@ -1025,11 +1025,10 @@ struct StateHeader {
 };
 constexpr uint64_t kStateMagic = 0x314554415453414dull;  // "MASTATE1"
 
-struct Piece {
-  void* dev;
-  size_t bytes;
-};
+}  // namespace
+}  // extern "C"
 
+namespace mam {
 std::vector<Piece> state_pieces(mam_problem* h) {
   const size_t MR = size_t(h->Mtot) * h->R;
   return {{h->theta, sizeof(float) * size_t(h->T) * h->ld},
@@ -1048,7 +1047,9 @@ std::vector<Piece> state_pieces(mam_problem* h) {
           {h->passes, sizeof(unsigned long long)},
           {h->iter_d, sizeof(long long)}};
 }
-}  // namespace
+}  // namespace mam
+
+extern "C" {
 
 mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes) {
   MAM_CHECK_HANDLE(h);

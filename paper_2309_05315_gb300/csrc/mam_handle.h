@@ -145,6 +145,13 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag);
 int avg_blocks(const mam_problem* h);
 size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c);
 void free_backward(mam_problem* h);
+
+// One device buffer of the iteration state (everything mam_get_state saves).
+struct Piece {
+  void* dev;
+  size_t bytes;
+};
+std::vector<Piece> state_pieces(mam_problem* h);
 mam_status reset_state(mam_problem* h);
 
 }  // namespace mam

@@ -1,0 +1,70 @@
+"""torch.autograd binding of the unrolled MAM barycenter (argument marshalling
+only).
+
+``MamFunction.apply(q, zeta, xi, S, alpha, rho, K, ckpt_every, theta0)``
+returns p^K, the barycenter estimate after K iterations of Algorithm 1 from
+theta^0 (balanced, deterministic, t = 1), as a float64 tensor on the device
+of ``q``.  Its backward pass is libmam's reverse sweep (mam_forward_record /
+mam_backward): gradients w.r.t. the weights q (unpruned order, zero for zero
+weights), the support points zeta and the barycenter points xi.  The inputs
+are copied to the host for mam_create, which copies them again; torch only
+supplies memory.
+"""
+from __future__ import annotations
+
+import math
+from types import SimpleNamespace
+
+import numpy as np
+import torch
+
+from .mam import Mam
+
+
+def _problem(q, zeta, xi, S, alpha, rho):
+    q = q.detach().to("cpu", torch.float64).numpy()
+    zeta = zeta.detach().to("cpu", torch.float64).numpy()
+    xi = xi.detach().to("cpu", torch.float64).numpy()
+    off = np.concatenate([[0], np.cumsum(S)]).astype(int)
+    return SimpleNamespace(
+        q=[q[off[m]:off[m + 1]] for m in range(len(S))],
+        zeta=[zeta[off[m]:off[m + 1]] for m in range(len(S))],
+        xi=xi, alpha=np.asarray(alpha, dtype=np.float64), rho=float(rho),
+        gamma=math.inf, n_bundles=1, cost=None)
+
+
+class MamFunction(torch.autograd.Function):
+    """p^K(q, zeta, xi) with libmam's checkpointed reverse sweep."""
+
+    @staticmethod
+    def forward(ctx, q, zeta, xi, S, alpha, rho=100.0, K=200, ckpt_every=20,
+                theta0="spread"):
+        prob = _problem(q, zeta, xi, S, alpha, rho)
+        mam = Mam(prob, cost_dtype="f32", theta0=theta0, diag="never")
+        mam.forward_record(int(K), int(ckpt_every))
+        p = torch.from_numpy(mam.barycenter()).to(q.device)
+        ctx.mam = mam
+        ctx.shapes = (q.shape, zeta.shape, xi.shape)
+        ctx.devices = (q.device, zeta.device, xi.device)
+        ctx.dtypes = (q.dtype, zeta.dtype, xi.dtype)
+        return p
+
+    @staticmethod
+    def backward(ctx, grad_p):
+        want = tuple(n for n, need in zip(("q", "zeta", "xi"), ctx.needs_input_grad[:3])
+                     if need)
+        gq, gz, gx = ctx.mam.backward(grad_p.detach().to("cpu", torch.float64).numpy(),
+                                      want=want)
+        ctx.mam.close()
+        out = []
+        for g, shp, dev, dt in zip((gq, gz, gx), ctx.shapes, ctx.devices, ctx.dtypes):
+            out.append(None if g is None else
+                       torch.from_numpy(np.asarray(g)).reshape(shp).to(dev, dt))
+        return (*out, None, None, None, None, None, None)
+
+
+def unrolled_barycenter(q, zeta, xi, S, alpha, rho=100.0, K=200, ckpt_every=20,
+                        theta0="spread"):
+    """Functional form of ``MamFunction.apply``."""
+    return MamFunction.apply(q, zeta, xi, list(S), list(alpha), rho, K, ckpt_every,
+                             theta0)

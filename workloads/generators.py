@@ -215,15 +215,20 @@ def config3(n_problems=256, i0=0, M_range=(4, 16)) -> List[Problem]:
     return out
 
 
-def config4(i=0) -> Problem:
-    """M=8 40x40 Gaussian mixtures; R=1600; target image for the loss."""
+def config4(i=0, grid=40, M=8) -> Problem:
+    """M=8 40x40 Gaussian mixtures; R=1600; target image for the loss.
+
+    ``grid`` and ``M`` shrink the same recipe (centres and widths scale with
+    the grid) for cases the FP64 reference finishes in seconds."""
     rng = np.random.default_rng(1000 * 4 + i)
-    imgs = [gaussian_mixture_image(rng, 40, 3, 5, 6, 34, 2.0, 6.0) for _ in range(8)]
+    f = grid / 40.0
+    imgs = [gaussian_mixture_image(rng, grid, 3, 5, 6 * f, 34 * f, 2.0 * f, 6.0 * f)
+            for _ in range(M)]
     trng = np.random.default_rng(1000 * 4 + i + 10**6)
-    tgt = gaussian_mixture_image(trng, 40, 3, 5, 6, 34, 2.0, 6.0).ravel()
+    tgt = gaussian_mixture_image(trng, grid, 3, 5, 6 * f, 34 * f, 2.0 * f, 6.0 * f).ravel()
     tgt = tgt / tgt.sum()
-    return problem_from_images("cfg4_mixture40_M8", imgs, rho=100.0, iters=200,
-                               target=tgt)
+    name = "cfg4_mixture40_M8" if (grid, M) == (40, 8) else f"cfg4_mixture{grid}_M{M}"
+    return problem_from_images(name, imgs, rho=100.0, iters=200, target=tgt)
 
 
 def config5(i=0, M=100) -> Problem:
