@@ -102,3 +102,19 @@ def test_is_nearest_point():
     d0 = np.sum((x[0] - w) ** 2)
     Y = rng.dirichlet(np.ones(6), size=20000)
     assert np.all(np.sum((Y - w) ** 2, axis=1) >= d0 - 1e-12)
+
+
+def test_hand_worked_examples():
+    """tests/golden/simplex_projection_examples.txt: projections worked by hand
+    from the KKT conditions."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "simplex_projection_examples.txt")
+    n = 0
+    for ln in open(path):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        tau, w, x = (part.split() for part in ln.split("|"))
+        got, _ = project_simplex(np.array([[float(v) for v in w]]), np.array([float(tau[0])]))
+        np.testing.assert_allclose(got[0], [float(v) for v in x], atol=1e-15)
+        n += 1
+    assert n == 5
