@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-gap", action="store_true",
+                    help="skip the time-to-gap (and, for the mixture workload, "
+                         "forward+backward) measurement")
     return ap.parse_args()
 
 
@@ -159,6 +162,53 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def time_to_gap(probs, cost_dtype, tol=1e-4, max_iters=20000, check_every=10):
+    """Wall time of mam_solve from theta^0 until the relative gap between the
+    objective of pi-hat and the dual lower bound of the current iterate (and,
+    when balanced, dist_L(pi-hat) / mass) is at most tol; the checks (one
+    diagnostic iteration and a host read every check_every iterations) are
+    inside the time."""
+    import torch
+    from paper_2309_05315_gb300 import Mam
+    kw = dict(cost_dtype=cost_dtype, diag="never")
+    g = Mam(problems=probs, **kw) if len(probs) > 1 else Mam(probs[0], **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, gap = g.solve(max_iters, tol, 0.0, check_every)
+    dt = time.perf_counter() - t0
+    g.close()
+    return {"tol": tol, "reached": bool(gap <= tol), "iterations": int(it), "seconds": dt,
+            "gap": gap, "check_every": check_every, "cost_dtype": cost_dtype,
+            "reference": "dual lower bound of the current iterate; balanced problems also "
+                         "need dist_L(pi-hat)/mass <= tol"}
+
+
+def forward_backward(prob, K=200, ckpt=20):
+    """Wall time of mam_forward_record(K, ckpt) + mam_backward for
+    L = ||p^K - target||^2 (host gradients), and of K plain iterations."""
+    import torch
+    from paper_2309_05315_gb300 import Mam
+    g = Mam(prob, cost_dtype="f32", diag="never")
+    g.forward_record(K, ckpt)           # warm-up (allocations, graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.forward_record(K, ckpt)
+    p = g.barycenter()
+    t1 = time.perf_counter()
+    g.backward(2.0 * (p - prob.target))
+    t2 = time.perf_counter()
+    g.set_state(g.get_state())
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    g.step(K)
+    g.barycenter()
+    t4 = time.perf_counter()
+    g.close()
+    return {"K": K, "ckpt_every": ckpt, "forward_record_s": t1 - t0, "backward_s": t2 - t1,
+            "fwd_bwd_s": t2 - t0, "plain_forward_s": t4 - t3,
+            "loss": float(np.sum((p - prob.target) ** 2))}
 
 
 def dist_env():
@@ -340,6 +390,11 @@ def main():
                                     "paper's datasets; see DESIGN.md)",
             "config": cfg, "roofline": roof, "gpu_launches": 2 * args.steps,
             "clocks": clocks}
+
+    if not args.no_gap:
+        line["time_to_gap"] = time_to_gap(probs, cost_dtype)
+        if args.workload == 4:
+            line["differentiation"] = forward_backward(probs[0])
 
     if not args.no_e2e:
         # End to end through the public API from host buffers: create (h2d of

@@ -34,8 +34,11 @@ struct BackwardState {
   float* stored = nullptr;   // [T][ld]
   double* pend = nullptr;    // [Mtot][R]
   double* acc_w = nullptr;   // [Mtot][R]
-  double* acc_t = nullptr;   // [Mtot][R]
-  double* acc_wz = nullptr;  // [Mtot][R][dim]
+  double* acc_prev = nullptr;  // [Mtot][R]
+  double* part = nullptr;    // [nchunks][1 + dim][R]
+  long long* chunk_begin = nullptr;  // [nchunks + 1]
+  int* meas_chunk = nullptr;         // [Mtot + 1]
+  int nchunks = 0;
   double* qbar = nullptr;    // [T]
   double* zetabar = nullptr; // [T][dim]
   double* xibar = nullptr;   // [R][dim]
@@ -158,9 +161,22 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   if (s == MAM_OK) s = balloc(h, b, &b->lam_seg, size_t(h->T) * b->ck, "stored thresholds");
   if (s == MAM_OK) s = balloc(h, b, &b->stored, Tl, "adjoint plan");
   if (s == MAM_OK) s = balloc(h, b, &b->pend, MR, "adjoint marginals");
+  // chunks of at most kBwdChunk consecutive columns of one measure
+  std::vector<long long> cb;
+  std::vector<int> mc;
+  for (int m = 0; m < h->Mtot; ++m) {
+    mc.push_back(int(cb.size()));
+    for (long long c = h->col_off[m]; c < h->col_off[m + 1]; c += kBwdChunk) cb.push_back(c);
+  }
+  mc.push_back(int(cb.size()));
+  b->nchunks = int(cb.size());
+  cb.push_back(h->col_off[h->Mtot]);
   if (s == MAM_OK) s = balloc(h, b, &b->acc_w, MR, "adjoint row sums");
-  if (s == MAM_OK) s = balloc(h, b, &b->acc_t, MR, "adjoint row sums");
-  if (s == MAM_OK) s = balloc(h, b, &b->acc_wz, MR * dim, "adjoint row moments");
+  if (s == MAM_OK) s = balloc(h, b, &b->acc_prev, MR, "adjoint row sums");
+  if (s == MAM_OK)
+    s = balloc(h, b, &b->part, size_t(b->nchunks) * (1 + dim) * h->R, "adjoint chunk sums");
+  if (s == MAM_OK) s = balloc(h, b, &b->chunk_begin, cb.size(), "chunk table");
+  if (s == MAM_OK) s = balloc(h, b, &b->meas_chunk, mc.size(), "chunk table");
   if (s == MAM_OK) s = balloc(h, b, &b->qbar, size_t(h->T), "grad q");
   if (s == MAM_OK) s = balloc(h, b, &b->zetabar, size_t(h->T) * dim, "grad zeta");
   if (s == MAM_OK) s = balloc(h, b, &b->xibar, size_t(h->R) * dim, "grad xi");
@@ -170,6 +186,11 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
     free_backward(h);
     return s;
   }
+  BWD_CUDA(cudaMemcpy(b->chunk_begin, cb.data(), sizeof(long long) * cb.size(),
+                      cudaMemcpyHostToDevice),
+           "chunk table upload");
+  BWD_CUDA(cudaMemcpy(b->meas_chunk, mc.data(), sizeof(int) * mc.size(), cudaMemcpyHostToDevice),
+           "chunk table upload");
   if (h->zeta_kept.size() == size_t(h->T) * h->dim && h->dim > 0)
     BWD_CUDA(cudaMemcpy(b->zeta, h->zeta_kept.data(), sizeof(double) * h->zeta_kept.size(),
                         cudaMemcpyHostToDevice),
@@ -215,9 +236,7 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
                            h->stream),
            "grad_p upload");
   BWD_CUDA(cudaMemsetAsync(b->stored, 0, sizeof(float) * Tl, h->stream), "memset");
-  BWD_CUDA(cudaMemsetAsync(b->acc_w, 0, sizeof(double) * MR, h->stream), "memset");
-  BWD_CUDA(cudaMemsetAsync(b->acc_t, 0, sizeof(double) * MR, h->stream), "memset");
-  BWD_CUDA(cudaMemsetAsync(b->acc_wz, 0, sizeof(double) * MR * dimA, h->stream), "memset");
+  BWD_CUDA(cudaMemsetAsync(b->acc_prev, 0, sizeof(double) * MR, h->stream), "memset");
   BWD_CUDA(cudaMemsetAsync(b->qbar, 0, sizeof(double) * h->T, h->stream), "memset");
   BWD_CUDA(cudaMemsetAsync(b->zetabar, 0, sizeof(double) * h->T * dimA, h->stream), "memset");
   BWD_CUDA(cudaMemsetAsync(b->xibar, 0, sizeof(double) * h->R * dimA, h->stream), "memset");
@@ -226,15 +245,17 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   A.stored = b->stored;
   A.pend = b->pend;
   A.col_meas = h->col_meas;
+  A.chunk_begin = b->chunk_begin;
+  A.meas_chunk = b->meas_chunk;
   A.zeta = b->zeta;
   A.xi = b->xi;
   A.alpha = h->alpha_d;
   A.Sd = h->Sd_d;
   A.a = h->a_d;
   A.irho = h->irho_m;
+  A.part = b->part;
   A.acc_w = b->acc_w;
-  A.acc_t = b->acc_t;
-  A.acc_wz = b->acc_wz;
+  A.acc_prev = b->acc_prev;
   A.qbar = b->qbar;
   A.zetabar = b->zetabar;
   A.xibar = b->xibar;
@@ -262,7 +283,7 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
       A.theta = b->th_seg + Tl * j;
       A.delta32 = b->d_seg + Ml * j;
       A.lam = b->lam_seg + size_t(h->T) * j;
-      BWD_CUDA(launch_bwd_step(h->cost_dtype, h->T, h->stream, A), "adjoint step");
+      BWD_CUDA(launch_bwd_step(h->cost_dtype, b->nchunks, h->stream, A), "adjoint step");
     }
   }
   if (h->theta0_mode == 0) BWD_CUDA(launch_bwd_theta0(h->T, h->stream, A), "adjoint theta0");

@@ -17,155 +17,212 @@
 //   zetabar_s += (2 alpha_m / rho) sum_r wbar_rs (xi_r - zeta_s),
 //   xibar_r   -= (2 alpha_m / rho) sum_s wbar_rs (xi_r - zeta_s).
 // thetabar is kept as a column-sparse part ("stored": wbar, zero off the
-// active set) plus a per-(measure,row) part ("pend": pbarm), which keeps every
-// row accumulation sparse.
+// active set) plus a per-(measure,row) part ("pend": pbarm).  Since the stored
+// part entering step k is the wbar of step k+1, sum_s thetabar'_rs =
+// (sum_s wbar^(k+1)_rs) + S_m pend_r: the row sums of one step are reused by
+// the next and no column is read twice.
+//
+// Layout of the work: a CTA owns a chunk of consecutive columns of one
+// measure and a thread owns fixed rows r = tid + i * blockDim.x of every
+// column of its chunk, so the per-row sums over the chunk (sum_s wbar_rs and
+// sum_s wbar_rs zeta_s) stay in registers.  Each chunk writes them once; the
+// row kernel adds the chunks of a measure in a fixed order.  No atomics, and
+// the result does not depend on scheduling.
 #include "mam_device.cuh"
 #include "mam_internal.h"
 
 namespace mam {
-
 namespace {
 
-constexpr int kBwdThreads = 256;
-
-__device__ __forceinline__ double block_sum_d(double v, double* sh) {
-  v = warp_sum_d(v);
+template <int N>
+__device__ __forceinline__ void block_sum_n(double (&v)[N], double (*sh)[4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < N; ++j) v[j] = warp_sum_d(v[j]);
+  __syncthreads();  // the previous call's readers are done
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) sh[warp][j] = v[j];
+  }
   __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
-  return t;
+  const int nw = int(blockDim.x >> 5);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[w][j];
+    v[j] = t;
+  }
 }
 
-template <int NVB, typename CT>
-__global__ void __launch_bounds__(kBwdThreads) bwd_column_kernel(const BwdArgs A) {
-  __shared__ double sh[32];
-  const long long col = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int m = A.col_meas[col];
-  const int R = A.R, ld = A.ld, dim = A.dim;
-  const float* th = A.theta + size_t(col) * ld;
-  const CT* c = static_cast<const CT*>(A.cost) + size_t(col) * ld;
-  const float* dl = A.delta32 + size_t(m) * ld;
-  float* st = A.stored + size_t(col) * ld;
-  const double* pd = A.pend + size_t(m) * R;
-  const float lam = A.lam[col];
+// One reverse step over the columns of chunk blockIdx.x.
+template <int NVB, typename CT, int DIM>
+__global__ void __launch_bounds__(kBwdMaxThreads) bwd_column_kernel(const BwdArgs A) {
+  __shared__ double sh[kBwdMaxThreads / 32][4];
+  constexpr int DZ = DIM > 0 ? DIM : 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long c0 = A.chunk_begin[blockIdx.x], c1 = A.chunk_begin[blockIdx.x + 1];
+  const int m = A.col_meas[c0];
+  const int R = A.R, ld = A.ld;
   const float irho = A.irho[m];
-  double tb[NVB];
-  float so[NVB];
-  bool act[NVB];
-  double s1 = 0.0, na = 0.0;
-#pragma unroll
-  for (int i = 0; i < NVB; ++i) {
-    const int r = tid + i * kBwdThreads;
-    act[i] = false;
-    tb[i] = 0.0;
-    so[i] = 0.f;
-    if (r < R) {
-      const float d = dl[r];  // t = 1: d = delta32 exactly
-      const float w = fmaf(-float(c[r]), irho, fmaf(2.f, d, th[r]));
-      act[i] = w > lam;
-      so[i] = st[r];
-      tb[i] = double(so[i]) + pd[r];
-      if (act[i]) {
-        s1 += tb[i];
-        na += 1.0;
-      }
-    }
-  }
-  s1 = block_sum_d(s1, sh);
-  na = block_sum_d(na, sh);
-  const double mean = na > 0 ? s1 / na : 0.0;
-  const double* zs = A.zeta + size_t(col) * dim;
-  double zx[3] = {0.0, 0.0, 0.0}, zw = 0.0;
-#pragma unroll
-  for (int i = 0; i < NVB; ++i) {
-    const int r = tid + i * kBwdThreads;
-    if (r >= R) continue;
-    const double wb = act[i] ? tb[i] - mean : 0.0;
-    st[r] = float(wb);
-    const size_t o = size_t(m) * R + r;
-    if (so[i] != 0.f) atomicAdd(A.acc_t + o, double(so[i]));
-    if (act[i]) {
-      atomicAdd(A.acc_w + o, wb);
-      for (int k = 0; k < dim; ++k) {
-        atomicAdd(A.acc_wz + o * dim + k, wb * zs[k]);
-        zx[k] += wb * A.xi[size_t(r) * dim + k];
-      }
-      zw += wb;
-    }
-  }
   const double coef = 2.0 * A.alpha[m] / A.rho;
-  double tot[3];
-  for (int k = 0; k < 3; ++k) tot[k] = (k < dim) ? block_sum_d(zx[k], sh) : 0.0;
-  const double zwt = block_sum_d(zw, sh);
-  if (tid == 0) {
-    A.qbar[col] += mean;
-    for (int k = 0; k < dim; ++k) A.zetabar[size_t(col) * dim + k] += coef * (tot[k] - zs[k] * zwt);
+  float d[NVB];
+  double pd[NVB], accW[NVB], accZ[NVB][DZ];
+#pragma unroll
+  for (int i = 0; i < NVB; ++i) {
+    const int r = tid + i * nt;
+    d[i] = r < R ? A.delta32[size_t(m) * ld + r] : 0.f;  // t = 1: d = delta32
+    pd[i] = r < R ? A.pend[size_t(m) * R + r] : 0.0;
+    accW[i] = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) accZ[i][k] = 0.0;
+  }
+  for (long long col = c0; col < c1; ++col) {
+    const float* th = A.theta + size_t(col) * ld;
+    const CT* c = static_cast<const CT*>(A.cost) + size_t(col) * ld;
+    float* st = A.stored + size_t(col) * ld;
+    const float lam = A.lam[col];
+    double tb[NVB];
+    bool act[NVB];
+    double v2[2] = {0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < NVB; ++i) {
+      const int r = tid + i * nt;
+      act[i] = false;
+      tb[i] = 0.0;
+      if (r < R) {
+        // w exactly as the forward column step formed it
+        const float w = fmaf(-float(c[r]), irho, fmaf(2.f, d[i], th[r]));
+        act[i] = w > lam;
+        tb[i] = double(st[r]) + pd[i];
+        if (act[i]) {
+          v2[0] += tb[i];
+          v2[1] += 1.0;
+        }
+      }
+    }
+    block_sum_n<2>(v2, sh);
+    const double mean = v2[1] > 0.0 ? v2[0] / v2[1] : 0.0;
+    double zs[DZ], zx[DZ];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      zs[k] = A.zeta[size_t(col) * DIM + k];
+      zx[k] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < NVB; ++i) {
+      const int r = tid + i * nt;
+      if (r >= R) continue;
+      const double wb = act[i] ? tb[i] - mean : 0.0;
+      st[r] = float(wb);
+      if (act[i]) {
+        accW[i] += wb;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          accZ[i][k] += wb * zs[k];
+          zx[k] += wb * (__ldg(A.xi + size_t(r) * DIM + k) - zs[k]);
+        }
+      }
+    }
+    if (DIM > 0) block_sum_n<DZ>(zx, sh);
+    if (tid == 0) {
+      A.qbar[col] += mean;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) A.zetabar[size_t(col) * DIM + k] += coef * zx[k];
+    }
+  }
+  // chunk partials, [chunk][1 + DIM][R]
+  double* part = A.part + size_t(blockIdx.x) * (1 + DIM) * R;
+#pragma unroll
+  for (int i = 0; i < NVB; ++i) {
+    const int r = tid + i * nt;
+    if (r >= R) continue;
+    part[r] = accW[i];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) part[size_t(1 + k) * R + r] = accZ[i][k];
   }
 }
 
 // Per row r: dbar, pbar, the new broadcast part of thetabar and xibar.
+// acc_prev holds sum_s wbar^(k+1)_rs (the stored part entering this step).
 __global__ void bwd_row_kernel(const BwdArgs A) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= A.R) return;
+  const int dim = A.dim, R = A.R;
   double pbar = 0.0;
   for (int m = 0; m < A.Mtot; ++m) {
-    const size_t o = size_t(m) * A.R + r;
-    const double dbar = 2.0 * A.acc_w[o] - (A.acc_t[o] + A.Sd[m] * A.pend[o]);
+    double w = 0.0;
+    for (int j = A.meas_chunk[m]; j < A.meas_chunk[m + 1]; ++j)
+      w += A.part[size_t(j) * (1 + dim) * R + r];
+    const size_t o = size_t(m) * R + r;
+    const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
+    A.acc_w[o] = w;
     pbar += dbar / A.Sd[m];
   }
   for (int m = 0; m < A.Mtot; ++m) {
-    const size_t o = size_t(m) * A.R + r;
-    const double dbar = 2.0 * A.acc_w[o] - (A.acc_t[o] + A.Sd[m] * A.pend[o]);
+    const size_t o = size_t(m) * R + r;
+    const double w = A.acc_w[o];
+    const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
     const double coef = 2.0 * A.alpha[m] / A.rho;
-    for (int k = 0; k < A.dim; ++k)
-      A.xibar[size_t(r) * A.dim + k] -=
-          coef * (A.xi[size_t(r) * A.dim + k] * A.acc_w[o] - A.acc_wz[o * A.dim + k]);
+    for (int k = 0; k < dim; ++k) {
+      double wz = 0.0;
+      for (int j = A.meas_chunk[m]; j < A.meas_chunk[m + 1]; ++j)
+        wz += A.part[(size_t(j) * (1 + dim) + 1 + k) * R + r];
+      A.xibar[size_t(r) * dim + k] -= coef * (A.xi[size_t(r) * dim + k] * w - wz);
+    }
     A.pend[o] = -dbar / A.Sd[m] + A.a[m] * pbar;
-    A.acc_w[o] = 0.0;
-    A.acc_t[o] = 0.0;
-    for (int k = 0; k < A.dim; ++k) A.acc_wz[o * A.dim + k] = 0.0;
+    A.acc_prev[o] = w;
   }
 }
 
 // theta^0_rs = q_s / R: qbar_s += sum_r thetabar^0_rs / R.
-__global__ void __launch_bounds__(kBwdThreads) bwd_theta0_kernel(const BwdArgs A) {
-  __shared__ double sh[32];
+__global__ void __launch_bounds__(256) bwd_theta0_kernel(const BwdArgs A) {
+  __shared__ double sh[8][4];
   const long long col = blockIdx.x;
   const int m = A.col_meas[col];
-  double s = 0.0;
+  double s[1] = {0.0};
   for (int r = threadIdx.x; r < A.R; r += blockDim.x)
-    s += double(A.stored[size_t(col) * A.ld + r]) + A.pend[size_t(m) * A.R + r];
-  s = block_sum_d(s, sh);
-  if (threadIdx.x == 0) A.qbar[col] += s / double(A.R);
+    s[0] += double(A.stored[size_t(col) * A.ld + r]) + A.pend[size_t(m) * A.R + r];
+  block_sum_n<1>(s, sh);
+  if (threadIdx.x == 0) A.qbar[col] += s[0] / double(A.R);
 }
 
-template <int NVB>
-cudaError_t bwd_col_nv(int dt, long long T, cudaStream_t st, const BwdArgs& a) {
+template <int NVB, int DIM>
+cudaError_t bwd_col_dt(int dt, int nchunks, int nt, cudaStream_t st, const BwdArgs& a) {
   switch (dt) {
-    case 0: bwd_column_kernel<NVB, float><<<unsigned(T), kBwdThreads, 0, st>>>(a); break;
-    case 1: bwd_column_kernel<NVB, __nv_bfloat16><<<unsigned(T), kBwdThreads, 0, st>>>(a); break;
-    case 2: bwd_column_kernel<NVB, __half><<<unsigned(T), kBwdThreads, 0, st>>>(a); break;
+    case 0: bwd_column_kernel<NVB, float, DIM><<<nchunks, nt, 0, st>>>(a); break;
+    case 1: bwd_column_kernel<NVB, __nv_bfloat16, DIM><<<nchunks, nt, 0, st>>>(a); break;
+    case 2: bwd_column_kernel<NVB, __half, DIM><<<nchunks, nt, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+template <int NVB>
+cudaError_t bwd_col_nv(int dt, int dim, int nchunks, int nt, cudaStream_t st, const BwdArgs& a) {
+  switch (dim) {
+    case 0: return bwd_col_dt<NVB, 0>(dt, nchunks, nt, st, a);
+    case 1: return bwd_col_dt<NVB, 1>(dt, nchunks, nt, st, a);
+    case 2: return bwd_col_dt<NVB, 2>(dt, nchunks, nt, st, a);
+    case 3: return bwd_col_dt<NVB, 3>(dt, nchunks, nt, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
-int bwd_max_rows() { return 16 * kBwdThreads; }
+int bwd_max_rows() { return 8 * kBwdMaxThreads; }
 
-cudaError_t launch_bwd_step(int cost_dtype, long long T, cudaStream_t st, const BwdArgs& a) {
-  const int need = (a.R + kBwdThreads - 1) / kBwdThreads;
+static int bwd_threads(int R) { return R <= 4 * 256 ? 256 : kBwdMaxThreads; }
+
+cudaError_t launch_bwd_step(int cost_dtype, int nchunks, cudaStream_t st, const BwdArgs& a) {
+  const int nt = bwd_threads(a.R);
+  const int need = (a.R + nt - 1) / nt;
   cudaError_t e;
-  if (need <= 1) e = bwd_col_nv<1>(cost_dtype, T, st, a);
-  else if (need <= 2) e = bwd_col_nv<2>(cost_dtype, T, st, a);
-  else if (need <= 4) e = bwd_col_nv<4>(cost_dtype, T, st, a);
-  else if (need <= 8) e = bwd_col_nv<8>(cost_dtype, T, st, a);
-  else if (need <= 16) e = bwd_col_nv<16>(cost_dtype, T, st, a);
+  if (need <= 1) e = bwd_col_nv<1>(cost_dtype, a.dim, nchunks, nt, st, a);
+  else if (need <= 2) e = bwd_col_nv<2>(cost_dtype, a.dim, nchunks, nt, st, a);
+  else if (need <= 4) e = bwd_col_nv<4>(cost_dtype, a.dim, nchunks, nt, st, a);
+  else if (need <= 6) e = bwd_col_nv<6>(cost_dtype, a.dim, nchunks, nt, st, a);
+  else if (need <= 8) e = bwd_col_nv<8>(cost_dtype, a.dim, nchunks, nt, st, a);
   else return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
   bwd_row_kernel<<<(a.R + 127) / 128, 128, 0, st>>>(a);
@@ -173,7 +230,7 @@ cudaError_t launch_bwd_step(int cost_dtype, long long T, cudaStream_t st, const 
 }
 
 cudaError_t launch_bwd_theta0(long long T, cudaStream_t st, const BwdArgs& a) {
-  bwd_theta0_kernel<<<unsigned(T), kBwdThreads, 0, st>>>(a);
+  bwd_theta0_kernel<<<unsigned(T), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -136,33 +136,38 @@ constexpr int kRedSlots = 32;  // warps per CTA, max
 
 // Reverse sweep through one balanced, deterministic iteration
 // (mam_backward_kernels.cu).  thetabar = stored (column-sparse) + pend
-// (broadcast along the columns of each measure).
+// (broadcast along the columns of each measure).  Columns are processed in
+// chunks of consecutive columns of one measure.
+constexpr int kBwdMaxThreads = 512;
+constexpr int kBwdChunk = 16;  // columns per chunk (at most)
 struct BwdArgs {
-  const float* theta;      // [T][ld] theta^k (the iterate the step read)
-  const void* cost;        // [T][ld]
-  const float* delta32;    // [Mtot][ld] (p - p^(m)) / S_m used by the step
-  const float* lam;        // [T] thresholds of the step
-  float* stored;           // [T][ld] sparse part of thetabar (in: k+1, out: k)
-  double* pend;            // [Mtot][R] broadcast part of thetabar
-  const int* col_meas;     // [T]
-  const double* zeta;      // [T][dim] kept support points
-  const double* xi;        // [R][dim]
-  const double* alpha;     // [Mtot]
-  const double* Sd;        // [Mtot]
-  const double* a;         // [Mtot]
-  const float* irho;       // [Mtot] FP32 1/rho, as in the forward column step
-  double* acc_w;           // [Mtot][R]  sum_s wbar_rs
-  double* acc_t;           // [Mtot][R]  sum_s stored_rs
-  double* acc_wz;          // [Mtot][R][dim]  sum_s wbar_rs zeta_s
-  double* qbar;            // [T]
-  double* zetabar;         // [T][dim]
-  double* xibar;           // [R][dim]
+  const float* theta;            // [T][ld] theta^k (the iterate the step read)
+  const void* cost;              // [T][ld]
+  const float* delta32;          // [Mtot][ld] (p - p^(m)) / S_m used by the step
+  const float* lam;              // [T] thresholds of the step
+  float* stored;                 // [T][ld] sparse part of thetabar (in: k+1, out: k)
+  double* pend;                  // [Mtot][R] broadcast part of thetabar
+  const int* col_meas;           // [T]
+  const long long* chunk_begin;  // [nchunks + 1] first column of each chunk
+  const int* meas_chunk;         // [Mtot + 1] first chunk of each measure
+  const double* zeta;            // [T][dim] kept support points
+  const double* xi;              // [R][dim]
+  const double* alpha;           // [Mtot]
+  const double* Sd;              // [Mtot]
+  const double* a;               // [Mtot]
+  const float* irho;             // [Mtot] FP32 1/rho, as in the forward column step
+  double* part;                  // [nchunks][1 + dim][R] chunk row sums of wbar, wbar zeta
+  double* acc_w;                 // [Mtot][R] sum_s wbar_rs of this step
+  double* acc_prev;              // [Mtot][R] sum_s wbar_rs of the step after (k+1)
+  double* qbar;                  // [T]
+  double* zetabar;               // [T][dim]
+  double* xibar;                 // [R][dim]
   int Mtot, R, ld, dim;
   double rho;
 };
 
 int bwd_max_rows();
-cudaError_t launch_bwd_step(int cost_dtype, long long T, cudaStream_t st, const BwdArgs& a);
+cudaError_t launch_bwd_step(int cost_dtype, int nchunks, cudaStream_t st, const BwdArgs& a);
 cudaError_t launch_bwd_theta0(long long T, cudaStream_t st, const BwdArgs& a);
 
 }  // namespace mam

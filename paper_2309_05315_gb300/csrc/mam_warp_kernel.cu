@@ -9,10 +9,14 @@
 //  * columns arrive through a ring of K shared-memory slots filled by
 //    bulk-async copies (cp.async.bulk, completion counted on one mbarrier per
 //    slot).  Warps claim columns in increasing order j; column j uses slot
-//    j mod K.  The warp that consumed column j refills the slot with column
-//    j + K as soon as it has read it.  With at most K warps per CTA, a slot
-//    is never claimed twice before its previous column was read, so the
-//    mbarrier phase of column j is always j / K;
+//    j mod K and is phase j / K of that slot's mbarrier.  The warp that
+//    consumed column j refills the slot with column j + K as soon as it has
+//    read it, and counts the refill in the slot's issue counter.  A warp that
+//    claims column j first waits until the counter shows that column j was
+//    issued: the warp holding column j - K may still be waiting for its data
+//    while other warps run ahead, and a parity wait started before phase
+//    j / K - 1 completed would pass on that older phase.  Every issued copy
+//    is therefore consumed before the CTA exits;
 //  * the shift d^(m) = t (p - p^(m)) / S_m is read through L1 from an FP32
 //    copy of (p - p^(m)) / S_m, so warps on different measures need no
 //    shared state.
@@ -135,6 +139,18 @@ __device__ __forceinline__ float warp_search(const float (&w)[NV][4], float tau,
   return lam_fin;
 }
 
+// Waits (bounded) until the shared counter *cnt reaches target.
+__device__ __forceinline__ bool wait_count_bounded(const int* cnt, int target,
+                                                   unsigned long long limit_ns) {
+  const volatile int* v = cnt;
+  if (*v >= target) return true;
+  const unsigned long long t0 = global_ns();
+  while (*v < target) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
 template <int NV, typename CT, bool DIAG>
 __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
     column_ring_kernel(const ColArgs A) {
@@ -185,6 +201,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
       bulk_load(th_s + size_t(s) * kSlot, A.theta + size_t(col) * ld, bytes_th, &full[s]);
       bulk_load(c_s + size_t(s) * kSlot, static_cast<const CT*>(A.cost) + size_t(col) * ld,
                 bytes_c, &full[s]);
+      __threadfence_block();  // the arrive and the copies precede the count
       atomicAdd(&issued_cnt[s], 1);
     };
     if (tid == 0)
@@ -201,7 +218,10 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
       const long long j = __shfl_sync(0xffffffffu, jj, 0);
       if (j >= ncol) break;
       const int s = int(j % K);
-      const bool ok = mbar_wait_bounded(&full[s], uint32_t((j / K) & 1), kWaitLimitNs);
+      bool ok = true;
+      if (lane == 0) ok = wait_count_bounded(&issued_cnt[s], int(j / K) + 1, kWaitLimitNs);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (ok) ok = mbar_wait_bounded(&full[s], uint32_t((j / K) & 1), kWaitLimitNs);
       if (!__all_sync(0xffffffffu, ok)) {
         failed = true;
         break;

@@ -72,17 +72,16 @@ def test_backward_ragged_rows_and_tail(Mam):
 
 
 def test_checkpoint_interval_does_not_change_gradients(Mam):
-    """The recomputed forward is bit-identical whatever the interval, so p^K
-    agrees exactly; the adjoint's row sums are FP64 atomic adds, whose order
-    varies from run to run, so the gradients agree to rounding."""
+    """The recomputed forward is bit-identical whatever the interval, and the
+    reverse sweep adds its row sums in a fixed order, so the gradients are
+    bit-identical too."""
     prob = config4(grid=16, M=3)
     K = 15
     ref = gpu_grads(Mam, prob, K, 1)
     for ck in (4, 15, 0):
         out = gpu_grads(Mam, prob, K, ck)
-        np.testing.assert_array_equal(out[0], ref[0])
-        for a, b in zip(ref[1:], out[1:]):
-            assert rel_l2(b, a) <= 1e-12
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b)
 
 
 def test_state_restored_after_backward(Mam):
@@ -121,6 +120,16 @@ def test_full_size_short_horizon(Mam):
     prob = config4()
     K = 4
     p, gq, gz, gx = gpu_grads(Mam, prob, K, 3)
+    _, oq, oz, ox = oracle_grads(prob, K)
+    for a, b in ((gq, oq), (gz, oz), (gx, ox)):
+        assert rel_l2(a, b) <= GRAD_TOL, rel_l2(a, b)
+
+
+def test_large_rows(Mam):
+    """R = 48 x 48 = 2304 takes the 512-thread reverse kernel."""
+    prob = config4(grid=48, M=2)
+    K = 3
+    p, gq, gz, gx = gpu_grads(Mam, prob, K, 2)
     _, oq, oz, ox = oracle_grads(prob, K)
     for a, b in ((gq, oq), (gz, oz), (gx, ox)):
         assert rel_l2(a, b) <= GRAD_TOL, rel_l2(a, b)

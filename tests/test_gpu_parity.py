@@ -166,9 +166,24 @@ def test_randomized_bundles(Mam):
     dict(kind=1, threads=128, vec=2, stages=8, ctas_per_sm=1),
     dict(kind=1, threads=224, vec=4, stages=7, ctas_per_sm=1),
     dict(kind=1, threads=64, vec=8, stages=3, ctas_per_sm=2),
+    dict(kind=1, threads=64, vec=2, stages=2, ctas_per_sm=8),
+    dict(kind=1, threads=256, vec=2, stages=8, ctas_per_sm=1),
 ])
 def test_kernel_configurations(Mam, cfg):
     compare_trajectory(Mam, config1(), 20, config=cfg)
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(kind=1, threads=256, vec=7, stages=8, ctas_per_sm=2),
+    dict(kind=1, threads=64, vec=8, stages=2, ctas_per_sm=4),
+    dict(kind=0, threads=64, vec=4, stages=3),
+])
+def test_ring_slots_on_stroke_images(Mam, cfg):
+    """R = 784 stroke images: as many warps as ring slots (every slot is
+    re-claimed as soon as it is refilled) and BF16 costs."""
+    from workloads import config3
+    prob = config3(1, i0=3)[0]
+    compare_trajectory(Mam, prob, 30, cost_dtype="bf16", oracle_cost="bf16", config=cfg)
 
 
 def test_cold_start_bisection_depths(Mam):
