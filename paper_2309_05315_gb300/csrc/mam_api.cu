@@ -229,32 +229,29 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
   return MAM_OK;
 }
 
-// The one-CTA-per-column kernel measured faster than the warp-per-column
-// ring on the R = 3600 workload (62 us vs 81 us per column step); the ring
-// stays available through mam_set_config / mam_autotune.
-constexpr bool kDefaultRing = false;
-
+// Default launch shape.  Columns of up to 2048 rows go to the
+// warp-per-column ring kernel (measured: 51 us vs 98 us per column step at
+// R = 1600, 0.72 ms vs 1.86 ms at R = 784 x 256 problems); longer columns to
+// the one-CTA-per-column kernel (62 us vs 81 us at R = 3600).
 mam_kernel_config default_config(const mam_problem* h) {
   const int ld4 = h->ld / 4;
-  if (kDefaultRing) {
-    // Columns that fit one warp (32 lanes x vec float4 groups): one warp per
-    // column, the narrowest compiled width that covers the column, as many
-    // ring slots as fit one CTA per SM, one warp per slot.
+  if (h->ld <= 2048) {
+    // The narrowest compiled width that covers the column, up to 12 ring
+    // slots (as many as fit in shared memory) and one warp per slot.
     const int need = (ld4 + 31) / 32;
-    for (int nv : {1, 2, 4, 7, 8, 13, 16, 24, 29, 32})
+    for (int nv : {1, 2, 4, 7, 8, 13, 16})
       if (nv >= need) {
         mam_kernel_config c{};
         c.kind = 1;
         c.vec = nv;
         const size_t slot = ring_kernel_smem(nv, 1, int(cost_elem_size(h->cost_dtype)));
-        int K = int((232448 - 64) / slot);
-        K = std::min(K, 32);
+        const int K = std::min(12, int((232448 - 64) / slot));
         const int W = std::min(K, ring_kernel_max_threads(nv) / 32);
         c.stages = K;
         c.threads = 32 * W;
-        c.ctas_per_sm = 1;
+        c.ctas_per_sm = 2;
         c.bisect_depth = 4;
-        if (W >= 1) return c;
+        if (W >= 1 && check_config(h, c) == MAM_OK) return c;
         break;
       }
   }
@@ -345,7 +342,6 @@ ColArgs col_args(const mam_problem* h) {
   a.nact = h->nact;
   a.col_meas = h->col_meas;
   a.col_off = h->col_off_d;
-  a.delta = h->delta;
   a.delta32 = h->delta32;
   a.blk = h->blk;
   a.nblk = avg_blocks(h);
@@ -378,10 +374,15 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   a.P = h->P;
   a.R = h->R;
   a.prob_meas = h->prob_meas_d;
-  a.Sd = h->Sd_d;
-  a.inv_S = h->invS_d;
+  a.S = h->S_d;
+  a.inv_S = h->invS_f;
+  a.inv_SF = h->invSF_d;
+  a.a_q = h->a_q_d;
   a.a = h->a_d;
+  a.inv_Sd = h->invS_d;
   a.acc = h->acc;
+  a.fx_f = float(h->fx_scale);
+  a.fx_inv_f = float(1.0 / h->fx_scale);
   a.fx_inv_scale = 1.0 / h->fx_scale;
   a.sched = h->sched_d;
   a.draw = draw_args(h);
@@ -391,7 +392,6 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   a.diag = diag;
   a.pm = h->pm;
   a.p = h->p;
-  a.delta = h->delta;
   a.delta32 = h->delta32;
   a.ld = h->ld;
   a.phat = h->phat;
@@ -427,7 +427,7 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
   if (diag && h->nb > 1) {
     // Lower bound of every measure for the v^k the column step just used
     // (the fused value covers only the drawn bundle).
-    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta, h->t_used, h->meas_prob,
+    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta32, h->t_used, h->meas_prob,
                        h->rho_m, h->col_meas, h->T, h->R, h->ld, h->diag_lb,
                        h->stream),
              "lower-bound kernel");
@@ -503,7 +503,7 @@ mam_status reset_state(mam_problem* h) {
   MAM_CUDA(launch_init_theta(h->theta, h->lam, h->nact, h->q64, h->T, h->R, h->ld,
                              h->theta0_mode, h->stream),
            "init kernel");
-  MAM_CUDA(launch_rowsum(h->theta, h->col_off_d, h->Mtot, h->R, h->ld, h->pm,
+  MAM_CUDA(launch_rowsum(h->theta, h->col_off_d, h->Mtot, h->R, h->ld, h->fx_scale, h->pm,
                          h->stream),
            "rowsum kernel");
   const size_t MR = size_t(h->Mtot) * h->R;
@@ -668,7 +668,9 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
       for (long long c = h->col_off[m]; c < h->col_off[m + 1]; ++c) Q += q64[c];
       qmax = std::max(qmax, Q);
     }
-    int e2 = 61 - int(std::ceil(std::log2(qmax * 1.0001)));
+    // 2 bits of headroom over the largest mass: the marginals p^(m) (row
+    // sums of theta = pihat - d) and p are held in the same fixed point.
+    int e2 = 59 - int(std::ceil(std::log2(qmax * 1.0001)));
     e2 = std::max(0, std::min(100, e2));
     h->fx_scale = std::ldexp(1.0, e2);
   }
@@ -691,7 +693,6 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->q64, size_t(h->T), "weights (fp64)");
   ALLOC(h->lam, size_t(h->T), "thresholds");
   ALLOC(h->pm, MR, "marginals");
-  ALLOC(h->delta, MR, "shifts");
   ALLOC(h->acc, MR, "row-sum accumulators");
   ALLOC(h->delta32, size_t(h->Mtot) * h->ld, "shifts (fp32)");
   ALLOC(h->phat, MR, "pi-hat marginals");
@@ -714,6 +715,9 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->S_d, size_t(h->Mtot), "sizes");
   ALLOC(h->Sd_d, size_t(h->Mtot), "sizes");
   ALLOC(h->invS_d, size_t(h->Mtot), "sizes");
+  ALLOC(h->invS_f, size_t(h->Mtot), "sizes");
+  ALLOC(h->invSF_d, size_t(h->Mtot), "sizes");
+  ALLOC(h->a_q_d, size_t(h->Mtot), "weights a");
   ALLOC(h->prob_meas_d, size_t(h->P) + 1, "problem table");
   ALLOC(h->rho_d, size_t(h->P), "rho");
   ALLOC(h->gamma_d, size_t(h->P), "gamma");
@@ -746,6 +750,16 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
     if ((s = upload(h, h->Sd_d, Sd.data(), Sd.size())) != MAM_OK) return bail(s);
     // (pageable sources: the copy has taken the data when the call returns)
     if ((s = upload(h, h->invS_d, iS.data(), iS.size())) != MAM_OK) return bail(s);
+    std::vector<float> iSf(h->Mtot), iSF(h->Mtot);
+    std::vector<long long> aq(h->Mtot);
+    for (int m = 0; m < h->Mtot; ++m) {
+      iSf[m] = float(iS[m]);
+      iSF[m] = float(iS[m] / h->fx_scale);
+      aq[m] = std::llround(std::ldexp(h->a[m], 62));
+    }
+    if ((s = upload(h, h->invS_f, iSf.data(), iSf.size())) != MAM_OK) return bail(s);
+    if ((s = upload(h, h->invSF_d, iSF.data(), iSF.size())) != MAM_OK) return bail(s);
+    if ((s = upload(h, h->a_q_d, aq.data(), aq.size())) != MAM_OK) return bail(s);
   }
   if ((s = upload(h, h->prob_meas_d, h->prob_meas.data(), h->prob_meas.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->rho_d, h->rho.data(), h->rho.size())) != MAM_OK) return bail(s);
@@ -979,11 +993,20 @@ mam_status mam_get_barycenter(mam_problem* h, double* p_out, int32_t device_ptr)
 mam_status mam_get_marginals(mam_problem* h, double* pm_out, int32_t device_ptr) {
   MAM_CHECK_HANDLE(h);
   if (!pm_out) return fail(h, MAM_ERR_INVALID_ARG, "pm_out is NULL");
-  MAM_CUDA(cudaMemcpyAsync(pm_out, h->pm, sizeof(double) * size_t(h->Mtot) * h->R,
-                           device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+  const size_t MR = size_t(h->Mtot) * h->R;
+  if (device_ptr) {
+    MAM_CUDA(launch_fx_to_double(h->pm, MR, 1.0 / h->fx_scale, pm_out, h->stream),
+             "marginal conversion");
+    return sync(h);
+  }
+  std::vector<long long> fx(MR);
+  MAM_CUDA(cudaMemcpyAsync(fx.data(), h->pm, sizeof(long long) * MR, cudaMemcpyDeviceToHost,
                            h->stream),
            "marginal copy");
-  return sync(h);
+  MAM_TRY(sync(h));
+  const double inv = 1.0 / h->fx_scale;
+  for (size_t i = 0; i < MR; ++i) pm_out[i] = double(fx[i]) * inv;
+  return MAM_OK;
 }
 
 mam_status mam_get_theta(mam_problem* h, float* theta_out) {
@@ -1023,7 +1046,7 @@ struct StateHeader {
   int32_t P, Mtot, R, ld;
   int32_t bundle_cur, bundle_prev, pad0, pad1;
 };
-constexpr uint64_t kStateMagic = 0x314554415453414dull;  // "MASTATE1"
+constexpr uint64_t kStateMagic = 0x324554415453414dull;  // "MASTATE2"
 
 }  // namespace
 }  // extern "C"
@@ -1034,9 +1057,8 @@ std::vector<Piece> state_pieces(mam_problem* h) {
   return {{h->theta, sizeof(float) * size_t(h->T) * h->ld},
           {h->lam, sizeof(float) * size_t(h->T)},
           {h->nact, sizeof(float) * size_t(h->T)},
-          {h->pm, sizeof(double) * MR},
+          {h->pm, sizeof(long long) * MR},
           {h->p, sizeof(double) * size_t(h->P) * h->R},
-          {h->delta, sizeof(double) * MR},
           {h->delta32, sizeof(float) * size_t(h->Mtot) * h->ld},
           {h->phat, sizeof(double) * MR},
           {h->t_used, sizeof(double) * h->P},

@@ -34,11 +34,13 @@
 namespace mam {
 namespace {
 
-template <int N>
-__device__ __forceinline__ void block_sum_n(double (&v)[N], double (*sh)[4]) {
+template <int N, typename V>
+__device__ __forceinline__ void block_sum_n(V (&v)[N], V (*sh)[4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < N; ++j) v[j] = warp_sum_d(v[j]);
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
   __syncthreads();  // the previous call's readers are done
   if (lane == 0) {
 #pragma unroll
@@ -48,16 +50,18 @@ __device__ __forceinline__ void block_sum_n(double (&v)[N], double (*sh)[4]) {
   const int nw = int(blockDim.x >> 5);
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    double t = 0.0;
+    V t = V(0);
     for (int w = 0; w < nw; ++w) t += sh[w][j];
     v[j] = t;
   }
 }
 
-// One reverse step over the columns of chunk blockIdx.x.
+// One reverse step over the columns of chunk blockIdx.x.  Per-entry
+// arithmetic is FP32 (the FP64 pipe of this GPU is a small fraction of its
+// FP32 rate); per-column and per-row results are accumulated in FP64.
 template <int NVB, typename CT, int DIM>
 __global__ void __launch_bounds__(kBwdMaxThreads) bwd_column_kernel(const BwdArgs A) {
-  __shared__ double sh[kBwdMaxThreads / 32][4];
+  __shared__ float sh[kBwdMaxThreads / 32][4];
   constexpr int DZ = DIM > 0 ? DIM : 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long c0 = A.chunk_begin[blockIdx.x], c1 = A.chunk_begin[blockIdx.x + 1];
@@ -65,69 +69,71 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_column_kernel(const BwdArg
   const int R = A.R, ld = A.ld;
   const float irho = A.irho[m];
   const double coef = 2.0 * A.alpha[m] / A.rho;
-  float d[NVB];
-  double pd[NVB], accW[NVB], accZ[NVB][DZ];
+  float d[NVB], pd[NVB], accW[NVB], accZ[NVB][DZ], xr[NVB][DZ];
 #pragma unroll
   for (int i = 0; i < NVB; ++i) {
     const int r = tid + i * nt;
     d[i] = r < R ? A.delta32[size_t(m) * ld + r] : 0.f;  // t = 1: d = delta32
-    pd[i] = r < R ? A.pend[size_t(m) * R + r] : 0.0;
-    accW[i] = 0.0;
+    pd[i] = r < R ? float(A.pend[size_t(m) * R + r]) : 0.f;
+    accW[i] = 0.f;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) accZ[i][k] = 0.0;
+    for (int k = 0; k < DIM; ++k) {
+      accZ[i][k] = 0.f;
+      xr[i][k] = r < R ? float(A.xi[size_t(r) * DIM + k]) : 0.f;
+    }
   }
   for (long long col = c0; col < c1; ++col) {
     const float* th = A.theta + size_t(col) * ld;
     const CT* c = static_cast<const CT*>(A.cost) + size_t(col) * ld;
     float* st = A.stored + size_t(col) * ld;
     const float lam = A.lam[col];
-    double tb[NVB];
+    float tb[NVB];
     bool act[NVB];
-    double v2[2] = {0.0, 0.0};
+    float v2[2] = {0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < NVB; ++i) {
       const int r = tid + i * nt;
       act[i] = false;
-      tb[i] = 0.0;
+      tb[i] = 0.f;
       if (r < R) {
         // w exactly as the forward column step formed it
         const float w = fmaf(-float(c[r]), irho, fmaf(2.f, d[i], th[r]));
         act[i] = w > lam;
-        tb[i] = double(st[r]) + pd[i];
+        tb[i] = st[r] + pd[i];
         if (act[i]) {
           v2[0] += tb[i];
-          v2[1] += 1.0;
+          v2[1] += 1.f;
         }
       }
     }
-    block_sum_n<2>(v2, sh);
-    const double mean = v2[1] > 0.0 ? v2[0] / v2[1] : 0.0;
-    double zs[DZ], zx[DZ];
+    block_sum_n<2, float>(v2, sh);
+    const float mean = v2[1] > 0.f ? v2[0] / v2[1] : 0.f;
+    float zs[DZ], zx[DZ];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      zs[k] = A.zeta[size_t(col) * DIM + k];
-      zx[k] = 0.0;
+      zs[k] = float(A.zeta[size_t(col) * DIM + k]);
+      zx[k] = 0.f;
     }
 #pragma unroll
     for (int i = 0; i < NVB; ++i) {
       const int r = tid + i * nt;
       if (r >= R) continue;
-      const double wb = act[i] ? tb[i] - mean : 0.0;
-      st[r] = float(wb);
+      const float wb = act[i] ? tb[i] - mean : 0.f;
+      st[r] = wb;
       if (act[i]) {
         accW[i] += wb;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-          accZ[i][k] += wb * zs[k];
-          zx[k] += wb * (__ldg(A.xi + size_t(r) * DIM + k) - zs[k]);
+          accZ[i][k] = fmaf(wb, zs[k], accZ[i][k]);
+          zx[k] = fmaf(wb, xr[i][k] - zs[k], zx[k]);
         }
       }
     }
-    if (DIM > 0) block_sum_n<DZ>(zx, sh);
+    if (DIM > 0) block_sum_n<DZ, float>(zx, sh);
     if (tid == 0) {
-      A.qbar[col] += mean;
+      A.qbar[col] += double(mean);
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) A.zetabar[size_t(col) * DIM + k] += coef * zx[k];
+      for (int k = 0; k < DIM; ++k) A.zetabar[size_t(col) * DIM + k] += coef * double(zx[k]);
     }
   }
   // chunk partials, [chunk][1 + DIM][R]
@@ -136,9 +142,9 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_column_kernel(const BwdArg
   for (int i = 0; i < NVB; ++i) {
     const int r = tid + i * nt;
     if (r >= R) continue;
-    part[r] = accW[i];
+    part[r] = double(accW[i]);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) part[size_t(1 + k) * R + r] = accZ[i][k];
+    for (int k = 0; k < DIM; ++k) part[size_t(1 + k) * R + r] = double(accZ[i][k]);
   }
 }
 
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(256) bwd_theta0_kernel(const BwdArgs A) {
   double s[1] = {0.0};
   for (int r = threadIdx.x; r < A.R; r += blockDim.x)
     s[0] += double(A.stored[size_t(col) * A.ld + r]) + A.pend[size_t(m) * A.R + r];
-  block_sum_n<1>(s, sh);
+  block_sum_n<1, double>(s, sh);
   if (threadIdx.x == 0) A.qbar[col] += s[0] / double(A.R);
 }
 

@@ -57,8 +57,7 @@ struct mam_problem {
   float* q = nullptr;
   double* q64 = nullptr;
   float* lam = nullptr;
-  double* pm = nullptr;
-  double* delta = nullptr;
+  long long* pm = nullptr;  // [Mtot][R] p^(m) in fixed point (scale fx_scale)
   float* delta32 = nullptr;
   double* phat = nullptr;
   double* p = nullptr;
@@ -80,6 +79,9 @@ struct mam_problem {
   int* S_d = nullptr;
   double* Sd_d = nullptr;
   double* invS_d = nullptr;
+  float* invS_f = nullptr;
+  float* invSF_d = nullptr;
+  long long* a_q_d = nullptr;
   int* prob_meas_d = nullptr;
   double* rho_d = nullptr;
   double* gamma_d = nullptr;

@@ -37,8 +37,7 @@ struct ColArgs {
   float* nact;               // [T] active-set size at that threshold (0: none)
   const int* col_meas;       // [T] measure of each column
   const long long* col_off;  // [Mtot+1] first column of each measure
-  const double* delta;       // [Mtot][R] (p - p^(m)) / S_m
-  const float* delta32;      // [Mtot][ld] the same in FP32, zero past R
+  const float* delta32;      // [Mtot][ld] (p - p^(m)) / S_m in FP32, zero past R
   const double* blk;         // [P][nblk][4] averaging block sums (dist^2 in [0])
   int nblk;
   const double* rho_p;       // [P]
@@ -66,24 +65,32 @@ struct ColArgs {
 
 // Arguments of the averaging kernel (Algorithm 1, Step 3 completion, Step 1
 // and the distance that fixes t^k).
+// Marginals are 64-bit fixed point with the scale F = 2^e of the row-sum
+// accumulators: integer adds and products are exact and order-independent,
+// and the FP64 pipe (a small fraction of the FP32 rate on this GPU) is left
+// to per-row work.
 struct AvgArgs {
   int P, R;
   const int* prob_meas;      // [P+1] first measure of each problem
-  const double* Sd;          // [Mtot] pruned support sizes S_m
-  const double* inv_S;       // [Mtot] 1 / S_m
-  const double* a;           // [Mtot] averaging weights of eq. (pr)
+  const int* S;              // [Mtot] pruned support sizes S_m
+  const float* inv_S;        // [Mtot] 1 / S_m
+  const float* inv_SF;       // [Mtot] 1 / (S_m F)
+  const long long* a_q;      // [Mtot] round(a_m 2^62), weights of eq. (pr)
+  const double* a;           // [Mtot] a_m (diagnostics)
+  const double* inv_Sd;      // [Mtot] 1 / S_m in FP64 (diagnostics)
   unsigned long long* acc;   // [Mtot][R] fixed-point sums of pi-hat (zeroed here)
-  double fx_inv_scale;       // 2^-e
+  float fx_f;                // F
+  float fx_inv_f;            // 1 / F
+  double fx_inv_scale;       // 1 / F
   const Sched* sched;
   Draw draw;
   const long long* iter;     // [1] completed column steps
   const double* t_used;      // [P] t of the column step just done
   int reduce;                // 1: p^(m) from acc; 0: p^(m) given
   int diag;                  // 1: also pi-hat marginals and their distance
-  double* pm;                // [Mtot][R]
+  long long* pm;             // [Mtot][R] p^(m) F
   double* p;                 // [P][R]
-  double* delta;             // [Mtot][R]
-  float* delta32;            // [Mtot][ld] FP32 copy the column kernels read
+  float* delta32;            // [Mtot][ld] (p - p^(m)) / S_m, read by the column kernels
   int ld;
   double* phat;              // [Mtot][R] row sums of pi-hat (DIAG)
   double* blk;               // [P][nblk][4] block sums: dist^2, dist_hat^2, |dp|^2
@@ -118,7 +125,8 @@ cudaError_t launch_init_theta(float* theta, float* lam, float* nact, const doubl
                               long long T, int R, int ld, int mode,
                               cudaStream_t st);
 cudaError_t launch_rowsum(const float* theta, const long long* col_off,
-                          int Mtot, int R, int ld, double* pm, cudaStream_t st);
+                          int Mtot, int R, int ld, double fx_scale, long long* pm,
+                          cudaStream_t st);
 cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                const float* res, const long long* prob_cols,
                                const Sched* sched, Draw draw,
@@ -126,10 +134,14 @@ cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                cudaStream_t st);
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
-                      const double* delta, const double* t_used,
+                      const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
                       float* diag_lb, cudaStream_t st);
+
+// out[i] = in[i] * scale (fixed-point marginals to FP64).
+cudaError_t launch_fx_to_double(const long long* in, size_t n, double scale, double* out,
+                                cudaStream_t st);
 
 constexpr int kRedSlots = 32;  // warps per CTA, max
 

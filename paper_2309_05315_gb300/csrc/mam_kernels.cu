@@ -370,102 +370,116 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
 
 // ------------------------------------------------------ average kernel
 
-// Step 3 completion and Step 1 of Algorithm 1, FP64:
+// Step 3 completion and Step 1 of Algorithm 1:
 //   p^(m)_r = sum_s pihat_rs - S_m d_r   (row sums of theta' = pihat - d)
 //   p = sum_m a_m p^(m)                  (eq. pr)
 //   delta^(m) = (p - p^(m)) / S_m        (the next column step uses t delta)
 // and the block sums of sum_m ||p - p^(m)||^2 / S_m (dist_L(theta)^2, which
 // fixes t^k), of the same for the pi-hat marginals (diagnostics) and of
-// ||p_new - p_old||^2.  Only the measures of the index set just processed
-// get new p^(m); the others keep theirs (Remark 2).  Block
-// (kAvgRows, kAvgSlices): threadIdx.x picks the row, threadIdx.y a slice of
-// the measures (m = m0 + y + k * kAvgSlices), so loads of different measures
-// are in flight together; slices are combined in shared memory in a fixed
-// order.  Grid (ceil(R/kAvgRows), P).
+// ||p_new - p_old||^2.  p^(m) and p are 64-bit fixed point (scale F = 2^e):
+// sum_s pihat arrives as an integer, d is an FP32 value whose product with F
+// is rounded to an integer, S_m d and the differences are exact, and
+// a_m p^(m) is a 64 x 64-bit product with a_m held to 2^-62.  Only the
+// measures of the index set just processed get new p^(m); the others keep
+// theirs (Remark 2).  Block (kAvgRows, kAvgSlices): threadIdx.x picks the
+// row, threadIdx.y a slice of the measures (m = m0 + y + k * kAvgSlices), so
+// loads of different measures are in flight together; slices are combined
+// in shared memory.  Grid (ceil(R/kAvgRows), P).
+__device__ __forceinline__ long long mul_q62(long long x, long long a) {
+  // floor(x * a / 2^62) for |x| < 2^63, 0 <= a <= 2^62 (exact)
+  const long long hi = __mul64hi(x, a);
+  const unsigned long long lo = (unsigned long long)x * (unsigned long long)a;
+  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
 __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
     average_kernel(const AvgArgs A) {
-  __shared__ double sp[kAvgSlices][kAvgRows];
+  __shared__ long long sp[kAvgSlices][kAvgRows];
   __shared__ double sq[kAvgSlices][kAvgRows];
-  __shared__ double sr[kAvgRows * kAvgSlices / 32][3];
+  __shared__ float se[kAvgRows * kAvgSlices / 32];
+  __shared__ double sr[kAvgRows * kAvgSlices / 32][2];
   pdl_wait();         // the column step's row sums and t are complete
   pdl_launch_next();  // the next column step may start copying its columns
   const int pr = blockIdx.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = blockIdx.x * kAvgRows + tx;
   const int m0 = A.prob_meas[pr], m1 = A.prob_meas[pr + 1];
-  const double t_old = A.t_used[pr];
+  const float t_old = float(A.t_used[pr]);
   const Sched sc = A.sched[draw_index_set(A.draw, *A.iter - 1)];
   const bool row = r < A.R;
   // pass 1: new marginals of this slice's measures, partial sums of a_m p^(m)
-  double ps = 0.0, phs = 0.0;
+  long long ps = 0;
+  double phs = 0.0;
   if (row) {
     for (int m = m0 + ty; m < m1; m += kAvgSlices) {
       const size_t o = size_t(m) * A.R + r;
-      double pmv;
+      long long pmv;
       if (A.reduce && m >= sc.meas_begin && m < sc.meas_end) {
-        const double sum_pihat = double((long long)A.acc[o]) * A.fx_inv_scale;
+        const long long sum_pihat = (long long)A.acc[o];
         A.acc[o] = 0ull;
         // the column kernel subtracted d = float(t delta) from every entry
-        const double d_used =
-            double(__fmul_rn(float(t_old), A.delta32[size_t(m) * A.ld + r]));
-        if (A.diag) A.phat[o] = sum_pihat;
-        pmv = sum_pihat - A.Sd[m] * d_used;
+        const float d_used = __fmul_rn(t_old, A.delta32[size_t(m) * A.ld + r]);
+        const long long d_fx = __float2ll_rn(d_used * A.fx_f);  // F = 2^e: exact scaling
+        if (A.diag) A.phat[o] = double(sum_pihat) * A.fx_inv_scale;
+        pmv = sum_pihat - (long long)A.S[m] * d_fx;
         A.pm[o] = pmv;
       } else {
         pmv = A.pm[o];
       }
-      ps += A.a[m] * pmv;
+      ps += mul_q62(pmv, A.a_q[m]);
       if (A.diag) phs += A.a[m] * A.phat[o];
     }
   }
   sp[ty][tx] = ps;
   sq[ty][tx] = phs;
   __syncthreads();
-  double p_new = 0.0, ph = 0.0;
+  long long p_fx = 0;
+  double ph = 0.0;
   for (int y = 0; y < kAvgSlices; ++y) {
-    p_new += sp[y][tx];
+    p_fx += sp[y][tx];
     ph += sq[y][tx];
   }
   // pass 2: shifts and the distance terms
-  double e = 0.0, eh = 0.0, dp2 = 0.0;
+  float e = 0.f;
+  double eh = 0.0, dp2 = 0.0;
   if (row) {
     for (int m = m0 + ty; m < m1; m += kAvgSlices) {
       const size_t o = size_t(m) * A.R + r;
-      const double df = p_new - A.pm[o];
-      const double is = A.inv_S[m];
-      const double dfs = df * is;
-      e += df * dfs;
-      A.delta[o] = dfs;
-      A.delta32[size_t(m) * A.ld + r] = float(dfs);
+      const float df = __ll2float_rn(p_fx - A.pm[o]);  // (p - p^(m)) F
+      A.delta32[size_t(m) * A.ld + r] = df * A.inv_SF[m];
+      const float dv = df * A.fx_inv_f;
+      e = fmaf(dv * dv, A.inv_S[m], e);
       if (A.diag) {
         const double dh = ph - A.phat[o];
-        eh += dh * dh * is;
+        eh += dh * dh * A.inv_Sd[m];
       }
     }
     if (ty == 0) {
       double* pp = A.p + size_t(pr) * A.R + r;
+      const double p_new = double(p_fx) * A.fx_inv_scale;
       const double dd = p_new - *pp;
       dp2 = dd * dd;
       *pp = p_new;
     }
   }
-  e = warp_sum_d(e);
-  eh = warp_sum_d(eh);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if (A.diag) eh = warp_sum_d(eh);
   dp2 = warp_sum_d(dp2);
   const int flat = ty * kAvgRows + tx;
   const int warp = flat >> 5, lane = flat & 31;
   if (lane == 0) {
-    sr[warp][0] = e;
-    sr[warp][1] = eh;
-    sr[warp][2] = dp2;
+    se[warp] = e;
+    sr[warp][0] = eh;
+    sr[warp][1] = dp2;
   }
   __syncthreads();
   if (flat == 0) {
     double b0 = 0, b1 = 0, b2 = 0;
     for (int i = 0; i < kAvgRows * kAvgSlices / 32; ++i) {
-      b0 += sr[i][0];
-      b1 += sr[i][1];
-      b2 += sr[i][2];
+      b0 += double(se[i]);
+      b1 += sr[i][0];
+      b2 += sr[i][1];
     }
     double* blk = A.blk + (size_t(pr) * gridDim.x + blockIdx.x) * 4;
     blk[0] = b0;
@@ -544,16 +558,17 @@ __global__ void init_theta_kernel(float* theta, float* lam, float* nact,
   }
 }
 
-// p^(m)_r = sum_s theta^(m)_rs in FP64 (Alg. 1 Step 0 and checkpoint restore).
+// p^(m)_r F = F sum_s theta^(m)_rs, summed in FP64 and rounded once to the
+// 64-bit fixed point of the marginals (Alg. 1 Step 0).
 __global__ void rowsum_kernel(const float* theta, const long long* col_off,
-                              int R, int ld, double* pm) {
+                              int R, int ld, double fx_scale, long long* pm) {
   const int m = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   double acc = 0.0;
   for (long long c = col_off[m]; c < col_off[m + 1]; ++c)
     acc += double(theta[size_t(c) * ld + r]);
-  pm[size_t(m) * R + r] = acc;
+  pm[size_t(m) * R + r] = __double2ll_rn(acc * fx_scale);
 }
 
 // Sums of the per-column diagnostics of problem blockIdx.x, FP64, fixed
@@ -606,7 +621,7 @@ __global__ void __launch_bounds__(256) diag_reduce_kernel(
 // One warp per column.
 template <typename CT>
 __global__ void __launch_bounds__(256) lb_kernel(
-    const CT* cost, const float* q, const double* delta, const double* t_used,
+    const CT* cost, const float* q, const float* delta32, const double* t_used,
     const int* meas_prob, const float* rho, const int* col_meas, long long T,
     int R, int ld, float* diag_lb) {
   const int lane = threadIdx.x & 31;
@@ -616,7 +631,7 @@ __global__ void __launch_bounds__(256) lb_kernel(
     const int m = col_meas[col];
     const float tt = float(t_used[meas_prob[m]]);
     const float rh = rho[m];
-    const double* dl = delta + size_t(m) * R;
+    const float* dl = delta32 + size_t(m) * ld;
     const CT* cc = cost + size_t(col) * ld;
     float mn = INFINITY;
     for (int r = lane; r < R; r += 32) {
@@ -624,7 +639,7 @@ __global__ void __launch_bounds__(256) lb_kernel(
       if constexpr (sizeof(CT) == 4) c = float(cc[r]);
       else if constexpr (std::is_same<CT, __half>::value) c = __half2float(cc[r]);
       else c = __bfloat162float(cc[r]);
-      mn = fminf(mn, c - rh * (tt * float(dl[r])));
+      mn = fminf(mn, c - rh * __fmul_rn(tt, dl[r]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -767,16 +782,31 @@ cudaError_t launch_init_theta(float* theta, float* lam, float* nact,
   return cudaGetLastError();
 }
 
+__global__ void fx_to_double_kernel(const long long* in, size_t n, double scale, double* out) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    out[i] = double(in[i]) * scale;
+}
+
+cudaError_t launch_fx_to_double(const long long* in, size_t n, double scale, double* out,
+                                cudaStream_t st) {
+  size_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  fx_to_double_kernel<<<unsigned(g), 256, 0, st>>>(in, n, scale, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rowsum(const float* theta, const long long* col_off,
-                          int Mtot, int R, int ld, double* pm,
+                          int Mtot, int R, int ld, double fx_scale, long long* pm,
                           cudaStream_t st) {
   rowsum_kernel<<<dim3((R + 127) / 128, Mtot), 128, 0, st>>>(theta, col_off, R,
-                                                             ld, pm);
+                                                             ld, fx_scale, pm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
-                      const double* delta, const double* t_used,
+                      const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
                       float* diag_lb, cudaStream_t st) {
@@ -785,13 +815,13 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
   if (g < 1) g = 1;
   switch (cost_dtype) {
     case 0:
-      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
       break;
     case 1:
-      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
       break;
     case 2:
-      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
       break;
     default:
       return cudaErrorInvalidValue;

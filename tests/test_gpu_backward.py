@@ -109,8 +109,9 @@ def test_sum_of_barycenter_closed_form(Mam):
         gq, gz, gx = g.backward(np.ones(g.R))
     expect = np.concatenate([np.where(np.asarray(prob.q[m]) > 0, prep.a[m], 0.0)
                              for m in range(prep.M)])
-    np.testing.assert_allclose(gq, expect, rtol=1e-9, atol=1e-12)
-    assert np.abs(gz).max() <= 1e-9 and np.abs(gx).max() <= 1e-9
+    # the reverse sweep works in FP32 per plan entry: FP32 rounding of a_m
+    np.testing.assert_allclose(gq, expect, rtol=1e-6, atol=1e-12)
+    assert np.abs(gz).max() <= 1e-7 and np.abs(gx).max() <= 1e-7
 
 
 def test_full_size_short_horizon(Mam):
@@ -137,13 +138,14 @@ def test_large_rows(Mam):
 
 def test_full_size_long_horizon_invariants(Mam):
     """K = 200, checkpoint every 20: translation invariance of the cost
-    (sum_s dL/dzeta_s + sum_r dL/dxi_r = 0) and finiteness."""
+    (sum_s dL/dzeta_s + sum_r dL/dxi_r = 0, to the FP32 rounding of the
+    per-entry products) and finiteness."""
     prob = config4()
     p, gq, gz, gx = gpu_grads(Mam, prob, 200, 20)
     assert np.all(np.isfinite(gq)) and np.all(np.isfinite(gz)) and np.all(np.isfinite(gx))
     tot = gz.sum(axis=0) + gx.sum(axis=0)
     scale = np.abs(gz).sum() + np.abs(gx).sum()
-    assert np.abs(tot).max() <= 1e-9 * scale
+    assert np.abs(tot).max() <= 1e-6 * scale
 
 
 def test_backward_rejections(Mam):
