@@ -396,10 +396,29 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   a.ld = h->ld;
   a.phat = h->phat;
   a.blk = h->blk;
+  a.slices = h->avg_slices;
   return a;
 }
 
-int avg_blocks(const mam_problem* h) { return (h->R + kAvgRows - 1) / kAvgRows; }
+int avg_blocks(const mam_problem* h) {
+  const int rows = kAvgThreads / h->avg_slices;
+  return (h->R + rows - 1) / rows;
+}
+
+// Measure slices of the averaging block: at most 8 measures per thread, and
+// enough blocks to give every SM two.
+static int choose_avg_slices(const mam_problem* h) {
+  int mmax = 1;
+  for (int i = 0; i < h->P; ++i) mmax = std::max(mmax, h->prob_meas[i + 1] - h->prob_meas[i]);
+  int sl = 1;
+  while (sl < 8 && (mmax + sl - 1) / sl > 8) sl *= 2;
+  while (sl < 8) {
+    const long long nblk = (h->R + kAvgThreads / sl - 1) / (kAvgThreads / sl);
+    if (nblk * h->P >= 2LL * std::max(1, h->num_sms)) break;
+    sl *= 2;
+  }
+  return sl;
+}
 
 static mam_status prof_event(mam_problem* h, cudaEvent_t* ev) {
   if (h->prof_used >= h->prof_events.size()) {
@@ -698,6 +717,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->phat, MR, "pi-hat marginals");
   ALLOC(h->p, size_t(h->P) * h->R, "barycenters");
   ALLOC(h->t_used, size_t(h->P), "t");
+  h->avg_slices = choose_avg_slices(h);
   ALLOC(h->blk, size_t(h->P) * avg_blocks(h) * 4, "block sums");
   ALLOC(h->done, 1, "arrival counter");
   ALLOC(h->nact, size_t(h->T), "active-set sizes");

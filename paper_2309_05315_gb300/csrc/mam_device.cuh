@@ -170,6 +170,37 @@ struct MaxThreads {
 
 // ------------------------------------------------------------ helpers
 
+// Conversions between FP32 and 64-bit integers with integer instructions
+// only (the hardware conversions run on the FP64 pipe, a small fraction of
+// the FP32 rate on this GPU).
+// f32_to_i64_rn: round to nearest, ties to even, for finite |x| < 2^63.
+__device__ __forceinline__ long long f32_to_i64_rn(float x) {
+  const unsigned u = __float_as_uint(x);
+  const int ex = int((u >> 23) & 0xffu);
+  if (ex < 126) return 0;  // |x| < 0.5, zero and subnormals included
+  const unsigned long long mant = (u & 0x7fffffu) | 0x800000u;
+  const int sh = ex - 150;  // |x| = mant * 2^sh
+  unsigned long long mag;
+  if (sh >= 0) {
+    mag = mant << sh;
+  } else {
+    const int r = -sh;  // 1..24
+    const unsigned long long q = mant >> r;
+    const unsigned long long rem = mant & ((1ull << r) - 1ull);
+    const unsigned long long half = 1ull << (r - 1);
+    mag = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  }
+  return (u >> 31) ? -(long long)mag : (long long)mag;
+}
+
+// i64_to_f32: v = hi 2^32 + lo, each half converted, then one fused
+// multiply-add (within about one unit in the last place).
+__device__ __forceinline__ float i64_to_f32(long long v) {
+  const int hi = int(v >> 32);
+  const unsigned lo = unsigned(v & 0xffffffffll);
+  return fmaf(float(hi), 4294967296.f, float(lo));
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

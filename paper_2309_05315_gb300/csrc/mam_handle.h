@@ -98,6 +98,7 @@ struct mam_problem {
   mam_kernel_config cfg{};
   int grid = 0;
   size_t smem = 0;
+  int avg_slices = 8;  // measure slices of the averaging block
   cudaGraphExec_t graph = nullptr;
 
   // host mirrors

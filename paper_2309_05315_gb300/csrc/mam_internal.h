@@ -94,10 +94,12 @@ struct AvgArgs {
   int ld;
   double* phat;              // [Mtot][R] row sums of pi-hat (DIAG)
   double* blk;               // [P][nblk][4] block sums: dist^2, dist_hat^2, |dp|^2
+  int slices;                // measure slices per block (1, 2, 4, 8)
 };
 
-constexpr int kAvgRows = 16;    // rows per averaging block
-constexpr int kAvgSlices = 8;   // measure slices per averaging block
+constexpr int kAvgThreads = 128;  // threads per averaging block: rows x measure slices
+constexpr int kAvgGroup = 4;      // measures whose loads an averaging thread batches
+constexpr int kAvgKeep = 16;      // marginals an averaging thread keeps in registers
 
 // Launch helpers (mam_kernels.cu).
 cudaError_t launch_column(int nv, int cost_dtype, bool diag, int grid, int threads,

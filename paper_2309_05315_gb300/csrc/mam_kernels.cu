@@ -5,7 +5,7 @@
 //                   M^k, fused with the row sums of Step 3 (order-independent
 //                   fixed-point accumulation) and with the diagnostics
 //                   (W-hat, lower bound, fixed-point residual).
-//   average_kernel  Step 3 completion (FP64), Step 1 (p = sum_m a_m p^(m),
+//   average_kernel  Step 3 completion (64-bit fixed point), Step 1 (p = sum_m a_m p^(m),
 //                   eq. pr) and the factor t^k.
 //
 // Plans theta and costs c are stored column-contiguous with a padded stride
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
           for (int e = 0; e < 4; ++e)
             if (pv[e] > 0.f)
               atomicAdd(acc_m + 4 * idx + e,
-                        (unsigned long long)__float2ll_rn(pv[e] * fx));
+                        (unsigned long long)f32_to_i64_rn(pv[e] * fx));
         }
         if (idx < ld4) {
           const float4 ov = make_float4(lo(o01), hi(o01), lo(o23), hi(o23));
@@ -379,12 +379,13 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
 // ||p_new - p_old||^2.  p^(m) and p are 64-bit fixed point (scale F = 2^e):
 // sum_s pihat arrives as an integer, d is an FP32 value whose product with F
 // is rounded to an integer, S_m d and the differences are exact, and
-// a_m p^(m) is a 64 x 64-bit product with a_m held to 2^-62.  Only the
-// measures of the index set just processed get new p^(m); the others keep
-// theirs (Remark 2).  Block (kAvgRows, kAvgSlices): threadIdx.x picks the
-// row, threadIdx.y a slice of the measures (m = m0 + y + k * kAvgSlices), so
-// loads of different measures are in flight together; slices are combined
-// in shared memory.  Grid (ceil(R/kAvgRows), P).
+// a_m p^(m) is a 64 x 64-bit product with a_m held to 2^-62; no per-(m, r)
+// step uses the FP64 pipe.  Only the measures of the index set just
+// processed get new p^(m); the others keep theirs (Remark 2).
+// Block (kAvgThreads / SL rows) x (SL measure slices): threadIdx.x picks the
+// row, threadIdx.y a slice of the measures (m = m0 + y + k SL), so each
+// thread walks several measures with independent loads; slices are combined
+// in shared memory.  Grid (ceil(R / rows), P).
 __device__ __forceinline__ long long mul_q62(long long x, long long a) {
   // floor(x * a / 2^62) for |x| < 2^63, 0 <= a <= 2^62 (exact)
   const long long hi = __mul64hi(x, a);
@@ -392,64 +393,133 @@ __device__ __forceinline__ long long mul_q62(long long x, long long a) {
   return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
 }
 
-__global__ void __launch_bounds__(kAvgRows * kAvgSlices)
-    average_kernel(const AvgArgs A) {
-  __shared__ long long sp[kAvgSlices][kAvgRows];
-  __shared__ double sq[kAvgSlices][kAvgRows];
-  __shared__ float se[kAvgRows * kAvgSlices / 32];
-  __shared__ double sr[kAvgRows * kAvgSlices / 32][2];
+template <int SL>
+__global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
+  constexpr int RX = kAvgThreads / SL;
+  constexpr int NW = kAvgThreads / 32;
+  __shared__ long long sp[SL][RX];
+  __shared__ double sq[SL][RX];
+  __shared__ float se[NW];
+  __shared__ double sr[NW][2];
+  __shared__ float t_sh;
   pdl_wait();         // the column step's row sums and t are complete
   pdl_launch_next();  // the next column step may start copying its columns
   const int pr = blockIdx.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int r = blockIdx.x * kAvgRows + tx;
+  const int flat = ty * RX + tx;
+  const int r = blockIdx.x * RX + tx;
   const int m0 = A.prob_meas[pr], m1 = A.prob_meas[pr + 1];
-  const float t_old = float(A.t_used[pr]);
+  if (flat == 0) t_sh = float(A.t_used[pr]);
   const Sched sc = A.sched[draw_index_set(A.draw, *A.iter - 1)];
   const bool row = r < A.R;
-  // pass 1: new marginals of this slice's measures, partial sums of a_m p^(m)
+  const bool diag = A.diag != 0;
+  __syncthreads();
+  const float t_old = t_sh;
+  // pass 1: new marginals of this slice's measures, partial sums of a_m p^(m).
+  // Measures go in groups of kAvgGroup whose loads are all issued before any
+  // store (the stores could alias later loads, which would serialise the L2
+  // round trips); the first kAvgKeep marginals stay in registers for pass 2.
+  const bool upd_all = A.reduce != 0;
   long long ps = 0;
   double phs = 0.0;
-  if (row) {
-    for (int m = m0 + ty; m < m1; m += kAvgSlices) {
-      const size_t o = size_t(m) * A.R + r;
-      long long pmv;
-      if (A.reduce && m >= sc.meas_begin && m < sc.meas_end) {
-        const long long sum_pihat = (long long)A.acc[o];
-        A.acc[o] = 0ull;
-        // the column kernel subtracted d = float(t delta) from every entry
-        const float d_used = __fmul_rn(t_old, A.delta32[size_t(m) * A.ld + r]);
-        const long long d_fx = __float2ll_rn(d_used * A.fx_f);  // F = 2^e: exact scaling
-        if (A.diag) A.phat[o] = double(sum_pihat) * A.fx_inv_scale;
-        pmv = sum_pihat - (long long)A.S[m] * d_fx;
-        A.pm[o] = pmv;
-      } else {
-        pmv = A.pm[o];
+  long long pmr[kAvgKeep];
+  const int mb = m0 + ty;
+  const int nk = row && mb < m1 ? (m1 - mb + SL - 1) / SL : 0;  // this thread's measures
+#pragma unroll
+  for (int k0 = 0; k0 < kAvgKeep; k0 += kAvgGroup) {
+    if (k0 >= nk) break;
+    long long av[kAvgGroup];
+    float dlv[kAvgGroup];
+#pragma unroll
+    for (int u = 0; u < kAvgGroup; ++u) {
+      const int m = mb + (k0 + u) * SL;
+      av[u] = 0;
+      dlv[u] = 0.f;
+      if (k0 + u < nk) {
+        const size_t o = size_t(m) * A.R + r;
+        const bool upd = upd_all && m >= sc.meas_begin && m < sc.meas_end;
+        av[u] = upd ? (long long)A.acc[o] : A.pm[o];
+        if (upd) dlv[u] = A.delta32[size_t(m) * A.ld + r];
       }
-      ps += mul_q62(pmv, A.a_q[m]);
-      if (A.diag) phs += A.a[m] * A.phat[o];
+    }
+#pragma unroll
+    for (int u = 0; u < kAvgGroup; ++u) {
+      const int m = mb + (k0 + u) * SL;
+      if (k0 + u < nk) {
+        const size_t o = size_t(m) * A.R + r;
+        const bool upd = upd_all && m >= sc.meas_begin && m < sc.meas_end;
+        long long pmv = av[u];
+        if (upd) {
+          A.acc[o] = 0ull;
+          // the column kernel subtracted d = float(t delta) from every entry
+          const float d_used = __fmul_rn(t_old, dlv[u]);
+          const long long d_fx = f32_to_i64_rn(d_used * A.fx_f);  // F = 2^e: exact scaling
+          if (diag) A.phat[o] = double(av[u]) * A.fx_inv_scale;
+          pmv = av[u] - (long long)__ldg(A.S + m) * d_fx;
+          A.pm[o] = pmv;
+        }
+        pmr[k0 + u] = pmv;
+        ps += mul_q62(pmv, __ldg(A.a_q + m));
+        if (diag) phs += A.a[m] * A.phat[o];
+      }
     }
   }
-  sp[ty][tx] = ps;
-  sq[ty][tx] = phs;
-  __syncthreads();
-  long long p_fx = 0;
-  double ph = 0.0;
-  for (int y = 0; y < kAvgSlices; ++y) {
-    p_fx += sp[y][tx];
-    ph += sq[y][tx];
+  for (int k = kAvgKeep; k < nk; ++k) {  // more measures than registers: plain loop
+    const int m = mb + k * SL;
+    const size_t o = size_t(m) * A.R + r;
+    long long pmv;
+    if (upd_all && m >= sc.meas_begin && m < sc.meas_end) {
+      const long long sum_pihat = (long long)A.acc[o];
+      A.acc[o] = 0ull;
+      const float d_used = __fmul_rn(t_old, A.delta32[size_t(m) * A.ld + r]);
+      const long long d_fx = f32_to_i64_rn(d_used * A.fx_f);
+      if (diag) A.phat[o] = double(sum_pihat) * A.fx_inv_scale;
+      pmv = sum_pihat - (long long)A.S[m] * d_fx;
+      A.pm[o] = pmv;
+    } else {
+      pmv = A.pm[o];
+    }
+    ps += mul_q62(pmv, A.a_q[m]);
+    if (diag) phs += A.a[m] * A.phat[o];
+  }
+  long long p_fx = ps;
+  double ph = phs;
+  if (SL > 1) {
+    sp[ty][tx] = ps;
+    if (diag) sq[ty][tx] = phs;
+    __syncthreads();
+    p_fx = 0;
+    ph = 0.0;
+#pragma unroll
+    for (int y = 0; y < SL; ++y) p_fx += sp[y][tx];
+    if (diag)
+      for (int y = 0; y < SL; ++y) ph += sq[y][tx];
   }
   // pass 2: shifts and the distance terms
   float e = 0.f;
   double eh = 0.0, dp2 = 0.0;
   if (row) {
-    for (int m = m0 + ty; m < m1; m += kAvgSlices) {
+#pragma unroll
+    for (int k = 0; k < kAvgKeep; ++k) {
+      if (k >= nk) break;
+      const int m = mb + k * SL;
+      const float df = i64_to_f32(p_fx - pmr[k]);  // (p - p^(m)) F
+      A.delta32[size_t(m) * A.ld + r] = df * __ldg(A.inv_SF + m);
+      const float dv = df * A.fx_inv_f;
+      e = fmaf(dv * dv, __ldg(A.inv_S + m), e);
+      if (diag) {
+        const double dh = ph - A.phat[size_t(m) * A.R + r];
+        eh += dh * dh * A.inv_Sd[m];
+      }
+    }
+    for (int k = kAvgKeep; k < nk; ++k) {
+      const int m = mb + k * SL;
       const size_t o = size_t(m) * A.R + r;
-      const float df = __ll2float_rn(p_fx - A.pm[o]);  // (p - p^(m)) F
+      const float df = i64_to_f32(p_fx - A.pm[o]);
       A.delta32[size_t(m) * A.ld + r] = df * A.inv_SF[m];
       const float dv = df * A.fx_inv_f;
       e = fmaf(dv * dv, A.inv_S[m], e);
-      if (A.diag) {
+      if (diag) {
         const double dh = ph - A.phat[o];
         eh += dh * dh * A.inv_Sd[m];
       }
@@ -462,12 +532,11 @@ __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
       *pp = p_new;
     }
   }
+  const int warp = flat >> 5, lane = flat & 31;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  if (A.diag) eh = warp_sum_d(eh);
-  dp2 = warp_sum_d(dp2);
-  const int flat = ty * kAvgRows + tx;
-  const int warp = flat >> 5, lane = flat & 31;
+  if (diag) eh = warp_sum_d(eh);
+  if (warp < (RX + 31) / 32) dp2 = warp_sum_d(dp2);  // only slice-0 rows carry dp2
   if (lane == 0) {
     se[warp] = e;
     sr[warp][0] = eh;
@@ -476,7 +545,7 @@ __global__ void __launch_bounds__(kAvgRows * kAvgSlices)
   __syncthreads();
   if (flat == 0) {
     double b0 = 0, b1 = 0, b2 = 0;
-    for (int i = 0; i < kAvgRows * kAvgSlices / 32; ++i) {
+    for (int i = 0; i < NW; ++i) {
       b0 += double(se[i]);
       b1 += sr[i][0];
       b2 += sr[i][1];
@@ -737,7 +806,13 @@ cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
 }
 
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st) {
-  return launch_pdl(average_kernel, dim3(nblk, a.P), dim3(kAvgRows, kAvgSlices), 0, st, a);
+  switch (a.slices) {
+    case 1: return launch_pdl(average_kernel<1>, dim3(nblk, a.P), dim3(kAvgThreads, 1), 0, st, a);
+    case 2: return launch_pdl(average_kernel<2>, dim3(nblk, a.P), dim3(kAvgThreads / 2, 2), 0, st, a);
+    case 4: return launch_pdl(average_kernel<4>, dim3(nblk, a.P), dim3(kAvgThreads / 4, 4), 0, st, a);
+    case 8: return launch_pdl(average_kernel<8>, dim3(nblk, a.P), dim3(kAvgThreads / 8, 8), 0, st, a);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
           for (int e = 0; e < 4; ++e)
             if (pv[e] > 0.f)
               atomicAdd(acc_m + 4 * g + e,
-                        (unsigned long long)__float2ll_rn(pv[e] * A.fx_scale));
+                        (unsigned long long)f32_to_i64_rn(pv[e] * A.fx_scale));
         }
         if (g < ld4) {
           if (DIAG) {
