@@ -33,7 +33,7 @@ struct BackwardState {
   float* lam_seg = nullptr;  // [ck][T]
   float* stored = nullptr;   // [T][ld]
   double* pend = nullptr;    // [Mtot][R]
-  double* acc_w = nullptr;   // [Mtot][R]
+  double* red = nullptr;     // [Mtot][1 + dim][R]
   double* acc_prev = nullptr;  // [Mtot][R]
   double* part = nullptr;    // [nchunks][1 + dim][R]
   long long* chunk_begin = nullptr;  // [nchunks + 1]
@@ -171,7 +171,7 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   mc.push_back(int(cb.size()));
   b->nchunks = int(cb.size());
   cb.push_back(h->col_off[h->Mtot]);
-  if (s == MAM_OK) s = balloc(h, b, &b->acc_w, MR, "adjoint row sums");
+  if (s == MAM_OK) s = balloc(h, b, &b->red, MR * (1 + dim), "adjoint row sums");
   if (s == MAM_OK) s = balloc(h, b, &b->acc_prev, MR, "adjoint row sums");
   if (s == MAM_OK)
     s = balloc(h, b, &b->part, size_t(b->nchunks) * (1 + dim) * h->R, "adjoint chunk sums");
@@ -251,10 +251,12 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   A.xi = b->xi;
   A.alpha = h->alpha_d;
   A.Sd = h->Sd_d;
+  A.inv_S = h->invS_d;
+  A.col_off = h->col_off_d;
   A.a = h->a_d;
   A.irho = h->irho_m;
   A.part = b->part;
-  A.acc_w = b->acc_w;
+  A.red = b->red;
   A.acc_prev = b->acc_prev;
   A.qbar = b->qbar;
   A.zetabar = b->zetabar;

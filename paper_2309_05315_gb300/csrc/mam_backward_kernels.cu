@@ -23,11 +23,15 @@
 // the next and no column is read twice.
 //
 // Layout of the work: a CTA owns a chunk of consecutive columns of one
-// measure and a thread owns fixed rows r = tid + i * blockDim.x of every
-// column of its chunk, so the per-row sums over the chunk (sum_s wbar_rs and
-// sum_s wbar_rs zeta_s) stay in registers.  Each chunk writes them once; the
-// row kernel adds the chunks of a measure in a fixed order.  No atomics, and
-// the result does not depend on scheduling.
+// measure.  Columns of up to 2048 rows go one per warp (bwd_warp_kernel),
+// and the per-row sums over the columns (sum_s wbar_rs and sum_s wbar_rs
+// zeta_s) are taken afterwards by a coalesced pass over the new stored part
+// (bwd_rowsum_kernel).  Longer columns go one per CTA, a thread owning fixed
+// rows r = tid + i * blockDim.x of every column of the chunk, which keeps
+// the per-row sums of the chunk in registers (bwd_column_kernel); the chunks
+// are then added per measure (bwd_chunk_reduce_kernel).  Every sum is taken
+// in a fixed order, without atomics, so the result does not depend on
+// scheduling.
 #include "mam_device.cuh"
 #include "mam_internal.h"
 
@@ -148,34 +152,188 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_column_kernel(const BwdArg
   }
 }
 
+// The same reverse step with one warp per column (columns of up to 64 x 32
+// rows); the warps of a CTA take the columns of its chunk in turn and reduce
+// with shuffles only.  Lane l holds rows r = l + 32 v (v < NV).  A first pass
+// over the column keeps only bit masks (active rows, rows whose stored value
+// is nonzero) and the sums for the mean; a second pass touches those rows
+// only, so register use stays low and the loads of the first pass overlap.
+// The per-row sums over the columns are left to bwd_rowsum_kernel.  The
+// first pass is branch-free, with the loads of G rows issued together.
+constexpr int kBwdWarps = 4;
+
+template <int NV, typename CT>
+__global__ void __launch_bounds__(kBwdWarps * 32) bwd_warp_kernel(const BwdArgs A) {
+  extern __shared__ float sm_w[];
+  const int R = A.R, ld = A.ld, dim = A.dim;
+  float* d_s = sm_w;       // [R] shift of the chunk's measure
+  float* pd_s = sm_w + R;  // [R] broadcast part of thetabar
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long c0 = A.chunk_begin[blockIdx.x], c1 = A.chunk_begin[blockIdx.x + 1];
+  const int m = A.col_meas[c0];
+  for (int i = tid; i < R; i += blockDim.x) {
+    d_s[i] = A.delta32[size_t(m) * ld + i];  // t = 1: d = delta32
+    pd_s[i] = float(A.pend[size_t(m) * R + i]);
+  }
+  __syncthreads();
+  const float irho = A.irho[m];
+  const double coef = 2.0 * A.alpha[m] / A.rho;
+  constexpr int G = 8;  // rows whose loads are issued together
+  for (long long col = c0 + warp; col < c1; col += kBwdWarps) {
+    const float* th = A.theta + size_t(col) * ld;
+    const CT* c = static_cast<const CT*>(A.cost) + size_t(col) * ld;
+    float* st = A.stored + size_t(col) * ld;
+    const float lam = A.lam[col];
+    unsigned long long act = 0ull, nz = 0ull;
+    float s1 = 0.f, na = 0.f;
+#pragma unroll
+    for (int v0 = 0; v0 < NV; v0 += G) {
+      float thv[G], cv[G], sv[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int r = lane + 32 * (v0 + u);
+        const bool ok = v0 + u < NV && r < R;
+        thv[u] = ok ? th[r] : 0.f;
+        cv[u] = ok ? float(c[r]) : INFINITY;
+        sv[u] = ok ? st[r] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int v = v0 + u;
+        const int r = lane + 32 * v;
+        if (v < NV && r < R) {
+          // w exactly as the forward column step formed it
+          const float w = fmaf(-cv[u], irho, fmaf(2.f, d_s[r], thv[u]));
+          const bool a = w > lam;
+          nz |= (unsigned long long)(sv[u] != 0.f) << v;
+          act |= (unsigned long long)a << v;
+          s1 += a ? sv[u] + pd_s[r] : 0.f;
+          na += a ? 1.f : 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      na += __shfl_xor_sync(0xffffffffu, na, o);
+    }
+    const float mean = na > 0.f ? s1 / na : 0.f;
+    float zs[3] = {0.f, 0.f, 0.f}, zx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < dim) zs[k] = float(A.zeta[size_t(col) * dim + k]);
+    unsigned long long todo = act | nz;
+    while (todo) {
+      const int v = __ffsll((long long)todo) - 1;
+      todo &= todo - 1ull;
+      const int r = lane + 32 * v;
+      if ((act >> v) & 1ull) {
+        const float wb = (st[r] + pd_s[r]) - mean;
+        st[r] = wb;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (k < dim) zx[k] = fmaf(wb, float(__ldg(A.xi + size_t(r) * dim + k)) - zs[k], zx[k]);
+      } else {
+        st[r] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < dim)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) zx[k] += __shfl_xor_sync(0xffffffffu, zx[k], o);
+    if (lane == 0) {
+      A.qbar[col] += double(mean);
+      for (int k = 0; k < dim; ++k) A.zetabar[size_t(col) * dim + k] += coef * double(zx[k]);
+    }
+  }
+}
+
+// Per-row sums of the new stored part over the columns of each measure, in a
+// fixed order: red[m][0][r] = sum_s wbar_rs, red[m][1 + k][r] =
+// sum_s wbar_rs zeta_s[k].  Block (kRsRows rows) x (kRsSlices column
+// slices), grid (rows, measures); coalesced row reads of the column-major
+// plan.
+constexpr int kRsRows = 32, kRsSlices = 16;
+__global__ void __launch_bounds__(kRsRows * kRsSlices) bwd_rowsum_kernel(const BwdArgs A) {
+  __shared__ float sh[4][kRsSlices][kRsRows];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r = blockIdx.x * kRsRows + tx;
+  const int m = blockIdx.y;
+  const int R = A.R, ld = A.ld, dim = A.dim, K1 = 1 + dim;
+  float sw = 0.f, sz[3] = {0.f, 0.f, 0.f};
+  if (r < R) {
+    const long long cb = A.col_off[m], ce = A.col_off[m + 1];
+#pragma unroll 8
+    for (long long col = cb + ty; col < ce; col += kRsSlices) {
+      const float wb = A.stored[size_t(col) * ld + r];
+      sw += wb;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < dim) sz[k] = fmaf(wb, float(__ldg(A.zeta + size_t(col) * dim + k)), sz[k]);
+    }
+  }
+  sh[0][ty][tx] = sw;
+  for (int k = 0; k < dim; ++k) sh[1 + k][ty][tx] = sz[k];
+  __syncthreads();
+  if (ty < K1 && r < R) {
+    double t = 0.0;
+#pragma unroll
+    for (int y = 0; y < kRsSlices; ++y) t += double(sh[ty][y][tx]);
+    A.red[(size_t(m) * K1 + ty) * R + r] = t;
+  }
+}
+
+// Sums the chunk partials of each measure in a fixed order:
+// red[m][k][r] = sum over the chunks j of measure m of part[j][k][r]
+// (k = 0: sum_s wbar_rs, k = 1..dim: sum_s wbar_rs zeta_s).  Block
+// (kRedRows rows) x (kRedSlices chunk slices), grid (rows, measures, 1 + dim).
+constexpr int kRedRows = 32, kRedSlices = 8;
+__global__ void __launch_bounds__(kRedRows * kRedSlices) bwd_chunk_reduce_kernel(const BwdArgs A) {
+  __shared__ double sh[kRedSlices][kRedRows];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r = blockIdx.x * kRedRows + tx;
+  const int m = blockIdx.y, k = blockIdx.z;
+  const int K1 = 1 + A.dim, R = A.R;
+  double s = 0.0;
+  if (r < R) {
+#pragma unroll 4
+    for (int j = A.meas_chunk[m] + ty; j < A.meas_chunk[m + 1]; j += kRedSlices)
+      s += A.part[(size_t(j) * K1 + k) * R + r];
+  }
+  sh[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && r < R) {
+    double t = 0.0;
+#pragma unroll
+    for (int y = 0; y < kRedSlices; ++y) t += sh[y][tx];
+    A.red[(size_t(m) * K1 + k) * R + r] = t;
+  }
+}
+
 // Per row r: dbar, pbar, the new broadcast part of thetabar and xibar.
 // acc_prev holds sum_s wbar^(k+1)_rs (the stored part entering this step).
 __global__ void bwd_row_kernel(const BwdArgs A) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= A.R) return;
-  const int dim = A.dim, R = A.R;
+  const int dim = A.dim, R = A.R, K1 = 1 + dim;
   double pbar = 0.0;
   for (int m = 0; m < A.Mtot; ++m) {
-    double w = 0.0;
-    for (int j = A.meas_chunk[m]; j < A.meas_chunk[m + 1]; ++j)
-      w += A.part[size_t(j) * (1 + dim) * R + r];
     const size_t o = size_t(m) * R + r;
+    const double w = A.red[size_t(m) * K1 * R + r];
     const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
-    A.acc_w[o] = w;
-    pbar += dbar / A.Sd[m];
+    pbar += dbar * A.inv_S[m];
   }
   for (int m = 0; m < A.Mtot; ++m) {
     const size_t o = size_t(m) * R + r;
-    const double w = A.acc_w[o];
+    const double w = A.red[size_t(m) * K1 * R + r];
     const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
     const double coef = 2.0 * A.alpha[m] / A.rho;
     for (int k = 0; k < dim; ++k) {
-      double wz = 0.0;
-      for (int j = A.meas_chunk[m]; j < A.meas_chunk[m + 1]; ++j)
-        wz += A.part[(size_t(j) * (1 + dim) + 1 + k) * R + r];
+      const double wz = A.red[(size_t(m) * K1 + 1 + k) * R + r];
       A.xibar[size_t(r) * dim + k] -= coef * (A.xi[size_t(r) * dim + k] * w - wz);
     }
-    A.pend[o] = -dbar / A.Sd[m] + A.a[m] * pbar;
+    A.pend[o] = -dbar * A.inv_S[m] + A.a[m] * pbar;
     A.acc_prev[o] = w;
   }
 }
@@ -218,20 +376,46 @@ cudaError_t bwd_col_nv(int dt, int dim, int nchunks, int nt, cudaStream_t st, co
 
 int bwd_max_rows() { return 8 * kBwdMaxThreads; }
 
-static int bwd_threads(int R) { return R <= 4 * 256 ? 256 : kBwdMaxThreads; }
+
+template <int NV>
+cudaError_t bwd_warp_nv(int dt, int nchunks, cudaStream_t st, const BwdArgs& a) {
+  const size_t smem = 2 * sizeof(float) * size_t(a.R);
+  switch (dt) {
+    case 0: bwd_warp_kernel<NV, float><<<nchunks, kBwdWarps * 32, smem, st>>>(a); break;
+    case 1: bwd_warp_kernel<NV, __nv_bfloat16><<<nchunks, kBwdWarps * 32, smem, st>>>(a); break;
+    case 2: bwd_warp_kernel<NV, __half><<<nchunks, kBwdWarps * 32, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bwd_rowsum_kernel<<<dim3((a.R + kRsRows - 1) / kRsRows, a.Mtot), dim3(kRsRows, kRsSlices), 0,
+                      st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bwd_step(int cost_dtype, int nchunks, cudaStream_t st, const BwdArgs& a) {
-  const int nt = bwd_threads(a.R);
-  const int need = (a.R + nt - 1) / nt;
+  const int nv = (a.R + 31) / 32;
   cudaError_t e;
-  if (need <= 1) e = bwd_col_nv<1>(cost_dtype, a.dim, nchunks, nt, st, a);
-  else if (need <= 2) e = bwd_col_nv<2>(cost_dtype, a.dim, nchunks, nt, st, a);
-  else if (need <= 4) e = bwd_col_nv<4>(cost_dtype, a.dim, nchunks, nt, st, a);
-  else if (need <= 6) e = bwd_col_nv<6>(cost_dtype, a.dim, nchunks, nt, st, a);
-  else if (need <= 8) e = bwd_col_nv<8>(cost_dtype, a.dim, nchunks, nt, st, a);
-  else return cudaErrorInvalidValue;
+  if (nv <= 4) e = bwd_warp_nv<4>(cost_dtype, nchunks, st, a);
+  else if (nv <= 8) e = bwd_warp_nv<8>(cost_dtype, nchunks, st, a);
+  else if (nv <= 16) e = bwd_warp_nv<16>(cost_dtype, nchunks, st, a);
+  else if (nv <= 25) e = bwd_warp_nv<25>(cost_dtype, nchunks, st, a);
+  else if (nv <= 32) e = bwd_warp_nv<32>(cost_dtype, nchunks, st, a);
+  else if (nv <= 50) e = bwd_warp_nv<50>(cost_dtype, nchunks, st, a);
+  else if (nv <= 64) e = bwd_warp_nv<64>(cost_dtype, nchunks, st, a);
+  else {
+    // longer columns (R > 2048): one CTA of 512 threads per chunk column
+    const int need = (a.R + kBwdMaxThreads - 1) / kBwdMaxThreads;
+    if (need <= 6) e = bwd_col_nv<6>(cost_dtype, a.dim, nchunks, kBwdMaxThreads, st, a);
+    else if (need <= 8) e = bwd_col_nv<8>(cost_dtype, a.dim, nchunks, kBwdMaxThreads, st, a);
+    else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
+    bwd_chunk_reduce_kernel<<<dim3((a.R + kRedRows - 1) / kRedRows, a.Mtot, 1 + a.dim),
+                              dim3(kRedRows, kRedSlices), 0, st>>>(a);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
-  bwd_row_kernel<<<(a.R + 127) / 128, 128, 0, st>>>(a);
+  bwd_row_kernel<<<(a.R + 63) / 64, 64, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -168,10 +168,12 @@ struct BwdArgs {
   const double* xi;              // [R][dim]
   const double* alpha;           // [Mtot]
   const double* Sd;              // [Mtot]
+  const double* inv_S;           // [Mtot] 1 / S_m
+  const long long* col_off;      // [Mtot + 1] first column of each measure
   const double* a;               // [Mtot]
   const float* irho;             // [Mtot] FP32 1/rho, as in the forward column step
   double* part;                  // [nchunks][1 + dim][R] chunk row sums of wbar, wbar zeta
-  double* acc_w;                 // [Mtot][R] sum_s wbar_rs of this step
+  double* red;                   // [Mtot][1 + dim][R] chunk sums added per measure
   double* acc_prev;              // [Mtot][R] sum_s wbar_rs of the step after (k+1)
   double* qbar;                  // [T]
   double* zetabar;               // [T][dim]
