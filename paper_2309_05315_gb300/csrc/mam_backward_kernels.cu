@@ -24,12 +24,11 @@
 //
 // Layout of the work: a CTA owns a chunk of consecutive columns of one
 // measure.  Columns of up to 2048 rows go one per warp (bwd_warp_kernel),
-// and the per-row sums over the columns (sum_s wbar_rs and sum_s wbar_rs
-// zeta_s) are taken afterwards by a coalesced pass over the new stored part
-// (bwd_rowsum_kernel).  Longer columns go one per CTA, a thread owning fixed
-// rows r = tid + i * blockDim.x of every column of the chunk, which keeps
-// the per-row sums of the chunk in registers (bwd_column_kernel); the chunks
-// are then added per measure (bwd_chunk_reduce_kernel).  Every sum is taken
+// and bwd_chunk_rowsum_kernel then takes each chunk's per-row sums (sum_s
+// wbar_rs and sum_s wbar_rs zeta_s) from the columns just written.  Longer columns go one per
+// CTA, a thread owning fixed rows r = tid + i * blockDim.x of every column of
+// the chunk, which keeps those sums in registers (bwd_column_kernel).  The
+// chunks are then added per measure (bwd_chunk_reduce_kernel).  Every sum is taken
 // in a fixed order, without atomics, so the result does not depend on
 // scheduling.
 #include "mam_device.cuh"
@@ -157,10 +156,10 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_column_kernel(const BwdArg
 // with shuffles only.  Lane l holds rows r = l + 32 v (v < NV).  A first pass
 // over the column keeps only bit masks (active rows, rows whose stored value
 // is nonzero) and the sums for the mean; a second pass touches those rows
-// only, so register use stays low and the loads of the first pass overlap.
-// The per-row sums over the columns are left to bwd_rowsum_kernel.  The
-// first pass is branch-free, with the loads of G rows issued together.
-constexpr int kBwdWarps = 4;
+// only, so register use stays low and the loads of the first pass overlap
+// (it is branch-free, with the loads of G rows issued together).  The
+// chunk's per-row sums are taken by bwd_chunk_rowsum_kernel.
+constexpr int kBwdWarps = 8;
 
 template <int NV, typename CT>
 __global__ void __launch_bounds__(kBwdWarps * 32) bwd_warp_kernel(const BwdArgs A) {
@@ -249,38 +248,48 @@ __global__ void __launch_bounds__(kBwdWarps * 32) bwd_warp_kernel(const BwdArgs 
   }
 }
 
-// Per-row sums of the new stored part over the columns of each measure, in a
-// fixed order: red[m][0][r] = sum_s wbar_rs, red[m][1 + k][r] =
-// sum_s wbar_rs zeta_s[k].  Block (kRsRows rows) x (kRsSlices column
-// slices), grid (rows, measures); coalesced row reads of the column-major
-// plan.
-constexpr int kRsRows = 32, kRsSlices = 16;
-__global__ void __launch_bounds__(kRsRows * kRsSlices) bwd_rowsum_kernel(const BwdArgs A) {
-  __shared__ float sh[4][kRsSlices][kRsRows];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int r = blockIdx.x * kRsRows + tx;
-  const int m = blockIdx.y;
-  const int R = A.R, ld = A.ld, dim = A.dim, K1 = 1 + dim;
-  float sw = 0.f, sz[3] = {0.f, 0.f, 0.f};
-  if (r < R) {
-    const long long cb = A.col_off[m], ce = A.col_off[m + 1];
-#pragma unroll 8
-    for (long long col = cb + ty; col < ce; col += kRsSlices) {
-      const float wb = A.stored[size_t(col) * ld + r];
-      sw += wb;
+// Per-row sums of one chunk's new stored part: part[chunk][0][r] = sum_s
+// wbar_rs, part[chunk][1 + k][r] = sum_s wbar_rs zeta_s[k], the columns added
+// in order.  A thread owns rows r = tid + i * kRsThreads (i < NVB), so every
+// column gives it NVB independent loads, and columns are unrolled by two.
+constexpr int kRsThreads = 256;
+
+template <int NVB>
+__global__ void __launch_bounds__(kRsThreads) bwd_chunk_rowsum_kernel(const BwdArgs A) {
+  const int tid = threadIdx.x;
+  const long long c0 = A.chunk_begin[blockIdx.x], c1 = A.chunk_begin[blockIdx.x + 1];
+  const int R = A.R, ld = A.ld, dim = A.dim;
+  float sw[NVB], sz[NVB][3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k < dim) sz[k] = fmaf(wb, float(__ldg(A.zeta + size_t(col) * dim + k)), sz[k]);
+  for (int i = 0; i < NVB; ++i) {
+    sw[i] = 0.f;
+    sz[i][0] = sz[i][1] = sz[i][2] = 0.f;
+  }
+#pragma unroll 2
+  for (long long col = c0; col < c1; ++col) {
+    const float* st = A.stored + size_t(col) * ld;
+    float zc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < dim) zc[k] = float(__ldg(A.zeta + size_t(col) * dim + k));
+#pragma unroll
+    for (int i = 0; i < NVB; ++i) {
+      const int r = tid + i * kRsThreads;
+      const float wb = r < R ? st[r] : 0.f;
+      sw[i] += wb;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sz[i][k] = fmaf(wb, zc[k], sz[i][k]);
     }
   }
-  sh[0][ty][tx] = sw;
-  for (int k = 0; k < dim; ++k) sh[1 + k][ty][tx] = sz[k];
-  __syncthreads();
-  if (ty < K1 && r < R) {
-    double t = 0.0;
+  double* part = A.part + size_t(blockIdx.x) * (1 + dim) * R;
 #pragma unroll
-    for (int y = 0; y < kRsSlices; ++y) t += double(sh[ty][y][tx]);
-    A.red[(size_t(m) * K1 + ty) * R + r] = t;
+  for (int i = 0; i < NVB; ++i) {
+    const int r = tid + i * kRsThreads;
+    if (r >= R) continue;
+    part[r] = double(sw[i]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < dim) part[size_t(1 + k) * R + r] = double(sz[i][k]);
   }
 }
 
@@ -377,6 +386,15 @@ cudaError_t bwd_col_nv(int dt, int dim, int nchunks, int nt, cudaStream_t st, co
 int bwd_max_rows() { return 8 * kBwdMaxThreads; }
 
 
+cudaError_t launch_chunk_rowsum(int nchunks, cudaStream_t st, const BwdArgs& a) {
+  const int need = (a.R + kRsThreads - 1) / kRsThreads;
+  if (need <= 2) bwd_chunk_rowsum_kernel<2><<<nchunks, kRsThreads, 0, st>>>(a);
+  else if (need <= 4) bwd_chunk_rowsum_kernel<4><<<nchunks, kRsThreads, 0, st>>>(a);
+  else if (need <= 8) bwd_chunk_rowsum_kernel<8><<<nchunks, kRsThreads, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 template <int NV>
 cudaError_t bwd_warp_nv(int dt, int nchunks, cudaStream_t st, const BwdArgs& a) {
   const size_t smem = 2 * sizeof(float) * size_t(a.R);
@@ -386,11 +404,9 @@ cudaError_t bwd_warp_nv(int dt, int nchunks, cudaStream_t st, const BwdArgs& a) 
     case 2: bwd_warp_kernel<NV, __half><<<nchunks, kBwdWarps * 32, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  bwd_rowsum_kernel<<<dim3((a.R + kRsRows - 1) / kRsRows, a.Mtot), dim3(kRsRows, kRsSlices), 0,
-                      st>>>(a);
-  return cudaGetLastError();
+  return launch_chunk_rowsum(nchunks, st, a);
 }
 
 cudaError_t launch_bwd_step(int cost_dtype, int nchunks, cudaStream_t st, const BwdArgs& a) {
@@ -409,12 +425,11 @@ cudaError_t launch_bwd_step(int cost_dtype, int nchunks, cudaStream_t st, const 
     if (need <= 6) e = bwd_col_nv<6>(cost_dtype, a.dim, nchunks, kBwdMaxThreads, st, a);
     else if (need <= 8) e = bwd_col_nv<8>(cost_dtype, a.dim, nchunks, kBwdMaxThreads, st, a);
     else return cudaErrorInvalidValue;
-    if (e != cudaSuccess) return e;
-    bwd_chunk_reduce_kernel<<<dim3((a.R + kRedRows - 1) / kRedRows, a.Mtot, 1 + a.dim),
-                              dim3(kRedRows, kRedSlices), 0, st>>>(a);
-    e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
+  bwd_chunk_reduce_kernel<<<dim3((a.R + kRedRows - 1) / kRedRows, a.Mtot, 1 + a.dim),
+                            dim3(kRedRows, kRedSlices), 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bwd_row_kernel<<<(a.R + 63) / 64, 64, 0, st>>>(a);
   return cudaGetLastError();
 }
