@@ -155,6 +155,10 @@ mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol,
 /* Diagnostics of problem `index` (0 for a single problem); synchronises. */
 mam_status mam_objective(mam_problem* h, int32_t index, mam_objective_t* out);
 
+/* Diagnostics of every problem of the handle at once, out[n_problems]
+ * (host array); synchronises.  Same values as mam_objective. */
+mam_status mam_objective_all(mam_problem* h, mam_objective_t* out);
+
 /* Barycenter p = sum_m a_m p^(m) of the current theta (Alg. 1 "Return"),
  * [n_problems][R] FP64.  device_ptr != 0: p_out is a device pointer. */
 mam_status mam_get_barycenter(mam_problem* h, double* p_out, int32_t device_ptr);

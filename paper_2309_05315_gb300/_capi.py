@@ -71,6 +71,7 @@ _SIGS = {
     "mam_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32,
                             C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "mam_objective": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(MamObjective)]),
+    "mam_objective_all": (C.c_int, [C.c_void_p, C.POINTER(MamObjective)]),
     "mam_get_barycenter": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "mam_get_theta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mam_get_marginals": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),

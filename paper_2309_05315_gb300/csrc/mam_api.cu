@@ -968,6 +968,21 @@ mam_status mam_objective(mam_problem* h, int32_t index, mam_objective_t* out) {
   return MAM_OK;
 }
 
+mam_status mam_objective_all(mam_problem* h, mam_objective_t* out) {
+  MAM_CHECK_HANDLE(h);
+  if (!out) return fail(h, MAM_ERR_INVALID_ARG, "out is NULL");
+  std::vector<mam_objective_t> all;
+  MAM_TRY(objective_all(h, all));
+  for (int i = 0; i < h->P; ++i) {
+    out[i] = all[i];
+    const double v[] = {all[i].w_hat, all[i].lower_bound, all[i].fp_resid,
+                        all[i].dist_pihat, all[i].dist_theta, all[i].t};
+    for (double x : v)
+      if (!std::isfinite(x)) return fail(h, MAM_ERR_NONFINITE, "non-finite diagnostic");
+  }
+  return MAM_OK;
+}
+
 mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol, double w_ref,
                      int32_t check_every, int32_t* iters_done, double* gap_out) {
   MAM_CHECK_HANDLE(h);

@@ -138,6 +138,12 @@ class Mam:
         self._check(_capi.lib().mam_objective(self._h, int(index), C.byref(o)))
         return o.as_dict()
 
+    def objectives(self) -> list:
+        """Diagnostics of every problem (one mam_objective_all call)."""
+        arr = (MamObjective * self.n_problems)()
+        self._check(_capi.lib().mam_objective_all(self._h, arr))
+        return [o.as_dict() for o in arr]
+
     # -- outputs
     def barycenter(self) -> np.ndarray:
         out = np.empty((self.n_problems, self.R), dtype=np.float64)

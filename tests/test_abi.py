@@ -94,6 +94,7 @@ def test_invalid_weights(L, q):
 def test_null_arguments(L):
     assert L.mam_step(None, 1) == 1
     assert L.mam_objective(None, 0, None) == 1
+    assert L.mam_objective_all(None, None) == 1
     assert L.mam_create(None, None) == 1
     L.mam_destroy(None)  # allowed
 

@@ -241,6 +241,7 @@ def test_batched_matches_separate_problems(Mam):
         batch.step(30)
         pb = batch.barycenter()
         objs = [batch.objective(i) for i in range(len(probs))]
+        assert batch.objectives() == objs  # mam_objective_all agrees with mam_objective
     for i, prob in enumerate(probs):
         prep = prepare(prob)
         orc = MamOracle(prep, prob.rho)
