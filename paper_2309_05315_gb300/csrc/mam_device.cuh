@@ -162,6 +162,17 @@ __device__ __forceinline__ void reduce3(float& a, float& b, float& c,
   rb ^= 1;
 }
 
+// Certificate for one warm Newton step l1 = l0 + dl from the threshold search:
+// gap0 = min_r |fl(w_r - l0)|.  When gap0 exceeds |dl| by more than the
+// rounding of w_r - l0 (at most 2^-24 |w_r - l0| relative) and of l0 + dl
+// (at most 2^-24 (|l0| + |dl|)), every w_r lies on the same side of l1 as of
+// l0, so the active set, and with it the exact threshold, is the one at l0's
+// Newton point: l1.  A w_r equal to l0 gives gap0 = 0 and no certificate.
+__device__ __forceinline__ bool newton_certified(float gap0, float dl, float l0) {
+  const float adl = fabsf(dl);
+  return gap0 * (1.f - 0x1p-20f) > adl + 0x1p-20f * (fabsf(l0) + adl);
+}
+
 template <int NV>
 struct MaxThreads {
   static constexpr int value = NV == 1 ? 1024 : NV == 2 ? 768

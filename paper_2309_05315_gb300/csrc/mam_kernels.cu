@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
       float lbmin = INFINITY;
       f2_t fa = 0ull, fb = 0ull;  // two packed accumulators
       float n = 0.f;
+      float gap0 = INFINITY;  // min_r |w_r - l0|: certificate of the warm Newton step
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int idx = v * nt + tid;
@@ -204,8 +205,11 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         const f2_t c01 = pk(c.x, c.y), c23 = pk(c.z, c.w);
         w2[v][0] = fma2(c01, nirho2, fma2(two2, d2[v][0], pk(th.x, th.y)));
         w2[v][1] = fma2(c23, nirho2, fma2(two2, d2[v][1], pk(th.z, th.w)));
-        fa = add2(fa, relu2(sub2(w2[v][0], l02), n));
-        fb = add2(fb, relu2(sub2(w2[v][1], l02), n));
+        const f2_t x0 = sub2(w2[v][0], l02), x1 = sub2(w2[v][1], l02);
+        gap0 = fminf(gap0, fminf(fminf(fabsf(lo(x0)), fabsf(hi(x0))),
+                                 fminf(fabsf(lo(x1)), fabsf(hi(x1)))));
+        fa = add2(fa, relu2(x0, n));
+        fb = add2(fb, relu2(x1, n));
         if (DIAG) {
           lbmin = fminf(lbmin, fminf(fminf(c.x - rho_m * lo(d2[v][0]), c.y - rho_m * hi(d2[v][0])),
                                      fminf(c.z - rho_m * lo(d2[v][1]), c.w - rho_m * hi(d2[v][1]))));
@@ -216,8 +220,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         const f2_t fs = add2(fa, fb);
         float f = lo(fs) + hi(fs);
         if (failed) f = -INFINITY;
-        float z = 0.f;
-        reduce3<false>(f, n, z, red, rb, lane, warp, nw);
+        reduce3<true>(f, n, gap0, red, rb, lane, warp, nw);
         if (!DIAG) refill(j);
         any_fail = !(f >= 0.f);
         fa = pk(f, 0.f);  // keep f (lo) for the search below
@@ -229,14 +232,24 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         float nprev = -1.f;
         bool bracket = !warm;
         float lam = l0;
+        bool done = false;
         if (warm) {
           if (n == 0.f) bracket = true;  // warm start at or above max w
           else {
-            lam = l0 + (f - tau) / n;
+            const float dl = (f - tau) / n;
+            lam = l0 + dl;
             nprev = n;
+            // No w_r between l0 and the Newton point (with a margin for the
+            // rounding of w - l0 and of l0 + dl): the active set at lam is the
+            // one at l0, so lam is the threshold -- the value the confirming
+            // pass below would return.
+            if (newton_certified(gap0, dl, l0)) {
+              lam_fin = lam;
+              done = true;
+            }
           }
         }
-        for (int it = 0; it < kMaxNewton; ++it) {
+        for (int it = 0; it < kMaxNewton && !done; ++it) {
           if (bracket) {  // lambda* lies in [max w - tau, max w)
             float mx = -INFINITY, z0 = 0.f, z1 = 0.f;
 #pragma unroll

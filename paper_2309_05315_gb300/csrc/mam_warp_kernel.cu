@@ -102,7 +102,36 @@ __device__ __forceinline__ float warp_search(const float (&w)[NV][4], float tau,
   float lam_fin = lam;
   float nprev = -1.f;
   bool bracket = !warm;
-  for (int it = 0; it < kMaxNewton; ++it) {
+  int it0 = 0;
+  if (warm) {  // first pass at the warm start, with the Newton-step certificate
+    float fs[4] = {0.f, 0.f, 0.f, 0.f}, ns[4] = {0.f, 0.f, 0.f, 0.f}, g = INFINITY;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float x = w[v][e] - lam;
+        fs[e] += fmaxf(x, 0.f);
+        ns[e] += x > 0.f ? 1.f : 0.f;
+        g = fminf(g, fabsf(x));
+      }
+    float f = (fs[0] + fs[1]) + (fs[2] + fs[3]);
+    float n = (ns[0] + ns[1]) + (ns[2] + ns[3]);
+    warp_sum2(f, n);
+    g = warp_min(g);
+    ++np;
+    it0 = 1;
+    if (n == 0.f) {
+      bracket = true;  // warm start at or above max w
+    } else {
+      const float dl = (f - tau) / n;
+      const float l0 = lam;
+      lam = lam + dl;
+      if (newton_certified(g, dl, l0)) return lam;  // same active set: exact
+      nprev = n;
+      lam_fin = lam;
+    }
+  }
+  for (int it = it0; it < kMaxNewton; ++it) {
     if (bracket) {
       float mx = -INFINITY;
 #pragma unroll
