@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--rho", type=float, default=None,
                     help="rho of the time-to-gap measurement (default: the workload's)")
     ap.add_argument("--gap-ref-iters", type=int, default=50000)
-    ap.add_argument("--no-gap", action="store_true",
-                    help="skip the time-to-gap (and, for the mixture workload, "
-                         "forward+backward) measurement")
+    ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap measurement")
+    ap.add_argument("--no-diff", action="store_true",
+                    help="mixture workload: skip the forward+backward measurement")
     return ap.parse_args()
 
 
@@ -446,8 +446,8 @@ def main():
         line["time_to_gap"] = time_to_gap(probs, cost_dtype, rho=args.rho,
                                           ref_iters=args.gap_ref_iters,
                                           max_iters=args.gap_ref_iters)
-        if args.workload == 4:
-            line["differentiation"] = forward_backward(probs[0])
+    if args.workload == 4 and not args.no_diff:
+        line["differentiation"] = forward_backward(probs[0])
 
     if not args.no_e2e:
         # End to end through the public API from host buffers: create (h2d of
