@@ -201,8 +201,8 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
  * kind 0: one CTA per column.  threads (multiple of 32, <= 1024) x vec
  *   (1..6 or 8) float4 groups cover the column; stages (2..4) is the depth
  *   of the bulk-copy pipeline.  Any R up to 12288.
- * kind 1: one warp per column.  vec (1,2,4,7,8,13,16,24,29,32) float4 groups
- *   per lane cover the column (R up to 4096); stages (>= threads/32) is the
+ * kind 1: one warp per column.  vec (1,2,4,7,8,13,16) float4 groups
+ *   per lane cover the column (R up to 2048); stages (>= threads/32) is the
  *   number of shared-memory ring slots; threads/32 warps per CTA.
  * ctas_per_sm: 0 = occupancy maximum.  bisect_depth (0..30): bisection steps
  * on a cold start.  Invalid combinations return MAM_ERR_INVALID_ARG. */

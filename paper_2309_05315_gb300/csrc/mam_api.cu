@@ -183,7 +183,7 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
   if (c.kind == 1) {  // one warp per column, shared-memory ring
     if (!ring_kernel_has(c.vec))
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
-                  "kind 1: vec must be one of 1,2,4,7,8,13,16,24,29,32");
+                  "kind 1: vec must be one of 1,2,4,7,8,13,16");
     if (c.threads < 32 || c.threads % 32 || c.threads > ring_kernel_max_threads(c.vec))
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
                   "kind 1: threads must be a multiple of 32 up to " +

@@ -342,7 +342,7 @@ mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best) 
         }
     }
   }
-  for (int nv : {1, 2, 4, 7, 8, 13, 16, 24, 29, 32}) {
+  for (int nv : {1, 2, 4, 7, 8, 13, 16}) {
     if (32 * nv * 4 < h->ld || 32 * nv * 4 > 2 * h->ld + 512) continue;
     for (int K : {2, 4, 7, 8, 12, 16, 24, 32})
       for (int W : {2, 4, 7, 8, 12, 16})

@@ -1,4 +1,4 @@
-// libmam: the column step with one warp per plan column (R up to 4096).
+// libmam: the column step with one warp per plan column (R up to 2048).
 //
 // Same mathematics as column_kernel in mam_kernels.cu (Algorithm 1, Step 2,
 // with the Step 3 row sums and the diagnostics), organised so that no CTA
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
   }
 }
 
-#define MAM_RING_NV_CASES(X) X(1) X(2) X(4) X(7) X(8) X(13) X(16) X(24) X(29) X(32)
+#define MAM_RING_NV_CASES(X) X(1) X(2) X(4) X(7) X(8) X(13) X(16)
 
 template <int NV, typename CT>
 cudaError_t ring_op(int op, bool diag, int grid, int threads, size_t smem,
