@@ -241,6 +241,7 @@ __device__ __forceinline__ int draw_index_set(const Draw& d, long long k) {
 // all of them obtain the same t.  Uses dred[0..31]; all threads must call.
 __device__ double t_from_blocks(const double* blk, int nblk, double rho,
                                 double gamma, double* dred, int tid, int nt) {
+  if (isinf(gamma)) return 1.0;  // balanced: t = 1 (uniform over the CTA)
   double acc = 0.0;
   for (int i = tid; i < nblk; i += nt) acc += blk[4 * i];
   acc = warp_sum_d(acc);

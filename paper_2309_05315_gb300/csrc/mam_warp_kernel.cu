@@ -54,6 +54,7 @@ __device__ __forceinline__ float warp_min(float a) {
 // t^k of Algorithm 1 for problem pr, evaluated by one warp from the
 // averaging kernel's block sums (fixed order: every warp gets the same t).
 __device__ __forceinline__ double warp_t(const ColArgs& A, int pr, int lane) {
+  if (isinf(A.gamma_p[pr])) return 1.0;  // balanced: t = 1
   const double* b = A.blk + size_t(pr) * A.nblk * 4;
   double acc = 0.0;
   for (int i = lane; i < A.nblk; i += 32) acc += b[4 * i];
