@@ -250,9 +250,12 @@ __device__ double t_from_blocks(const double* blk, int nblk, double rho,
   double tot = 0.0;
   for (int w = 0; w < (nt >> 5); ++w) tot += dred[w];
   __syncthreads();
-  const double D = sqrt(tot);
-  if (isinf(gamma) || rho * D <= gamma) return 1.0;
-  return gamma / (rho * D);
+  // sqrt and quotient in FP32 (the FP64 ones are long sequences on the slow
+  // FP64 pipe); t carries about 1e-7 relative error, the same in every CTA.
+  const float D = sqrtf(float(tot));
+  const float rD = float(rho) * D;
+  if (rD <= float(gamma)) return 1.0;
+  return double(__fdiv_rn(float(gamma), rD));
 }
 
 // ------------------------------------------------------- packed FP32 pairs

@@ -59,10 +59,12 @@ __device__ __forceinline__ double warp_t(const ColArgs& A, int pr, int lane) {
   double acc = 0.0;
   for (int i = lane; i < A.nblk; i += 32) acc += b[4 * i];
   acc = warp_sum_d(acc);
-  const double D = sqrt(acc);
-  const double rho = A.rho_p[pr], gamma = A.gamma_p[pr];
-  if (isinf(gamma) || rho * D <= gamma) return 1.0;
-  return gamma / (rho * D);
+  // as t_from_blocks: sqrt and quotient in FP32, identical in every warp
+  const float D = sqrtf(float(acc));
+  const float rD = float(A.rho_p[pr]) * D;
+  const float gamma = float(A.gamma_p[pr]);
+  if (rD <= gamma) return 1.0;
+  return double(__fdiv_rn(gamma, rD));
 }
 
 // Sum of max(w - l, 0) and #{w > l} over this lane's rows (independent
