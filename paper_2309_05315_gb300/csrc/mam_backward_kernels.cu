@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) bwd_warp_kernel(const BwdArgs 
 // Per-row sums of one chunk's new stored part: part[chunk][0][r] = sum_s
 // wbar_rs, part[chunk][1 + k][r] = sum_s wbar_rs zeta_s[k], the columns added
 // in order.  A thread owns rows r = tid + i * kRsThreads (i < NVB), so every
-// column gives it NVB independent loads, and columns are unrolled by two.
+// column gives it NVB independent loads, and columns are unrolled by four.
 constexpr int kRsThreads = 256;
 
 template <int NVB>
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kRsThreads) bwd_chunk_rowsum_kernel(const BwdA
     sw[i] = 0.f;
     sz[i][0] = sz[i][1] = sz[i][2] = 0.f;
   }
-#pragma unroll 2
+#pragma unroll 4
   for (long long col = c0; col < c1; ++col) {
     const float* st = A.stored + size_t(col) * ld;
     float zc[3] = {0.f, 0.f, 0.f};
