@@ -343,6 +343,8 @@ ColArgs col_args(const mam_problem* h) {
   a.col_meas = h->col_meas;
   a.col_off = h->col_off_d;
   a.delta32 = h->delta32;
+  a.amask = h->amask;
+  a.mw = (h->ld + 31) / 32;
   a.blk = h->blk;
   a.nblk = avg_blocks(h);
   a.rho_p = h->rho_d;

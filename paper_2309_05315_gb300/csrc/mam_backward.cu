@@ -5,11 +5,11 @@
 // every ckpt_every iterations (and after the last one).  mam_backward walks
 // the segments from the last to the first: it restores the segment's
 // snapshot, re-runs its iterations with the same kernels (the iterates are
-// bit-identical because every reduction is order-independent), keeping the
-// iterate theta^k, the shift (p - p^(m)) / S_m and the thresholds lambda^k of
-// each step, and then applies the reverse step of each iteration in reverse
-// order (mam_backward_kernels.cu).  Memory: (K / ckpt_every + 1) state
-// snapshots plus ckpt_every stored iterates.
+// bit-identical because every reduction is order-independent) while the
+// column kernels record each step's active sets as bit masks, and then
+// applies the reverse step of each iteration in reverse order
+// (mam_backward_kernels.cu).  Memory: (K / ckpt_every + 1) state snapshots
+// plus (ckpt_every + 1) active-set masks of one bit per plan entry.
 #include "mam.h"
 #include "mam_handle.h"
 #include "mam_internal.h"
@@ -28,9 +28,8 @@ struct BackwardState {
   size_t snap_bytes = 0;
   std::vector<char*> snaps;  // [nseg + 1]
   std::vector<long long> snap_iter, snap_diag_iter;
-  float* th_seg = nullptr;   // [ck][T][ld]
-  float* d_seg = nullptr;    // [ck][Mtot][ld]
-  float* lam_seg = nullptr;  // [ck][T]
+  unsigned* mask_seg = nullptr;   // [ck][T][mw] active sets of the segment's steps
+  unsigned* mask_next = nullptr;  // [T][mw] active sets of the step after the segment
   float* stored = nullptr;   // [T][ld]
   double* pend = nullptr;    // [Mtot][R]
   double* red = nullptr;     // [Mtot][1 + dim][R]
@@ -132,9 +131,6 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
     return fail(h, MAM_ERR_INVALID_ARG, "differentiation needs the deterministic index set");
   if (h->theta0_mode != 0 && h->theta0_mode != 1)
     return fail(h, MAM_ERR_INVALID_ARG, "theta0_mode must be 0 or 1");
-  if (h->R > bwd_max_rows())
-    return fail(h, MAM_ERR_INVALID_ARG,
-                "differentiation supports R <= " + std::to_string(bwd_max_rows()));
   if (K < 1) return fail(h, MAM_ERR_INVALID_ARG, "K must be >= 1");
   if (ckpt_every == 0) ckpt_every = std::max(1, int(std::lround(std::sqrt(double(K)))));
   if (ckpt_every < 1 || ckpt_every > K)
@@ -150,15 +146,15 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   b->snaps.assign(b->nseg + 1, nullptr);
   b->snap_iter.assign(b->nseg + 1, 0);
   b->snap_diag_iter.assign(b->nseg + 1, -1);
-  const size_t Tl = size_t(h->T) * h->ld, Ml = size_t(h->Mtot) * h->ld;
+  const size_t Tl = size_t(h->T) * h->ld;
   const size_t MR = size_t(h->Mtot) * h->R;
   const int dim = std::max(1, h->dim);
   mam_status s = MAM_OK;
   for (int i = 0; i <= b->nseg && s == MAM_OK; ++i)
     s = balloc(h, b, &b->snaps[i], b->snap_bytes, "state snapshot");
-  if (s == MAM_OK) s = balloc(h, b, &b->th_seg, Tl * b->ck, "stored iterates");
-  if (s == MAM_OK) s = balloc(h, b, &b->d_seg, Ml * b->ck, "stored shifts");
-  if (s == MAM_OK) s = balloc(h, b, &b->lam_seg, size_t(h->T) * b->ck, "stored thresholds");
+  const size_t Tm = size_t(h->T) * ((h->ld + 31) / 32);
+  if (s == MAM_OK) s = balloc(h, b, &b->mask_seg, Tm * b->ck, "active sets");
+  if (s == MAM_OK) s = balloc(h, b, &b->mask_next, Tm, "active sets");
   if (s == MAM_OK) s = balloc(h, b, &b->stored, Tl, "adjoint plan");
   if (s == MAM_OK) s = balloc(h, b, &b->pend, MR, "adjoint marginals");
   // chunks of at most kBwdChunk consecutive columns of one measure
@@ -223,7 +219,7 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   if ((grad_zeta || grad_xi) && !coords)
     return fail(h, MAM_ERR_INVALID_ARG,
                 "coordinate gradients need the squared Euclidean cost built from xi and zeta");
-  const size_t Tl = size_t(h->T) * h->ld, Ml = size_t(h->Mtot) * h->ld;
+  const size_t Tl = size_t(h->T) * h->ld;
   const size_t MR = size_t(h->Mtot) * h->R;
   const int dim = coords ? h->dim : 0;
   const int dimA = std::max(1, h->dim);
@@ -241,7 +237,6 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   BWD_CUDA(cudaMemsetAsync(b->zetabar, 0, sizeof(double) * h->T * dimA, h->stream), "memset");
   BWD_CUDA(cudaMemsetAsync(b->xibar, 0, sizeof(double) * h->R * dimA, h->stream), "memset");
   BwdArgs A{};
-  A.cost = h->cost;
   A.stored = b->stored;
   A.pend = b->pend;
   A.col_meas = h->col_meas;
@@ -252,9 +247,7 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   A.alpha = h->alpha_d;
   A.Sd = h->Sd_d;
   A.inv_S = h->invS_d;
-  A.col_off = h->col_off_d;
   A.a = h->a_d;
-  A.irho = h->irho_m;
   A.part = b->part;
   A.red = b->red;
   A.acc_prev = b->acc_prev;
@@ -266,27 +259,28 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   A.ld = h->ld;
   A.dim = dim;
   A.rho = h->rho[0];
+  A.mw = (h->ld + 31) / 32;
+  const size_t Tm = size_t(h->T) * A.mw;
+  bool have_next = false;  // the step after the segment exists (its sets are in mask_next)
   for (int seg = b->nseg - 1; seg >= 0; --seg) {
     BWD_TRY(restore(h, seg));
     const int L = std::min(b->ck, b->K - seg * b->ck);
+    // Re-run the segment; the column kernels record each step's active sets.
     for (int j = 0; j < L; ++j) {
-      BWD_CUDA(cudaMemcpyAsync(b->th_seg + Tl * j, h->theta, sizeof(float) * Tl,
-                               cudaMemcpyDeviceToDevice, h->stream),
-               "iterate copy");
-      BWD_CUDA(cudaMemcpyAsync(b->d_seg + Ml * j, h->delta32, sizeof(float) * Ml,
-                               cudaMemcpyDeviceToDevice, h->stream),
-               "shift copy");
-      BWD_TRY(launch_iteration(h, false));
-      BWD_CUDA(cudaMemcpyAsync(b->lam_seg + size_t(h->T) * j, h->lam, sizeof(float) * h->T,
-                               cudaMemcpyDeviceToDevice, h->stream),
-               "threshold copy");
+      h->amask = b->mask_seg + Tm * j;
+      const mam_status st = launch_iteration(h, false);
+      h->amask = nullptr;
+      BWD_TRY(st);
     }
     for (int j = L - 1; j >= 0; --j) {
-      A.theta = b->th_seg + Tl * j;
-      A.delta32 = b->d_seg + Ml * j;
-      A.lam = b->lam_seg + size_t(h->T) * j;
-      BWD_CUDA(launch_bwd_step(h->cost_dtype, b->nchunks, h->stream, A), "adjoint step");
+      A.am = b->mask_seg + Tm * j;
+      A.nm = j + 1 < L ? b->mask_seg + Tm * (j + 1) : (have_next ? b->mask_next : nullptr);
+      BWD_CUDA(launch_bwd_step(b->nchunks, h->stream, A), "adjoint step");
     }
+    BWD_CUDA(cudaMemcpyAsync(b->mask_next, b->mask_seg, sizeof(unsigned) * Tm,
+                             cudaMemcpyDeviceToDevice, h->stream),
+             "active-set copy");
+    have_next = true;
   }
   if (h->theta0_mode == 0) BWD_CUDA(launch_bwd_theta0(h->T, h->stream, A), "adjoint theta0");
   std::vector<double> qb(h->T), zb(size_t(h->T) * dimA), xb(size_t(h->R) * dimA);

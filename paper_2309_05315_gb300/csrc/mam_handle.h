@@ -111,6 +111,7 @@ struct mam_problem {
   size_t prof_used = 0;
 
   mam::BackwardState* bwd = nullptr;
+  unsigned* amask = nullptr;  // set during the reverse sweep's recomputation only
 };
 
 namespace mam {

@@ -38,6 +38,8 @@ struct ColArgs {
   const int* col_meas;       // [T] measure of each column
   const long long* col_off;  // [Mtot+1] first column of each measure
   const float* delta32;      // [Mtot][ld] (p - p^(m)) / S_m in FP32, zero past R
+  unsigned* amask;           // optional [T][mw] active-set bits (row r: word r/32, bit r%32)
+  int mw;                    // 32-bit words per column of amask
   const double* blk;         // [P][nblk][4] averaging block sums (dist^2 in [0])
   int nblk;
   const double* rho_p;       // [P]
@@ -152,13 +154,12 @@ constexpr int kRedSlots = 32;  // warps per CTA, max
 // (mam_backward_kernels.cu).  thetabar = stored (column-sparse) + pend
 // (broadcast along the columns of each measure).  Columns are processed in
 // chunks of consecutive columns of one measure.
-constexpr int kBwdMaxThreads = 512;
 constexpr int kBwdChunk = 16;  // columns per chunk (at most)
 struct BwdArgs {
-  const float* theta;            // [T][ld] theta^k (the iterate the step read)
-  const void* cost;              // [T][ld]
-  const float* delta32;          // [Mtot][ld] (p - p^(m)) / S_m used by the step
-  const float* lam;              // [T] thresholds of the step
+  const unsigned* am;            // [T][mw] active-set bits of the step
+  const unsigned* nm;            // [T][mw] active-set bits of the step after, or
+                                 // nullptr (the stored part entering is zero)
+  int mw;                        // words per column
   float* stored;                 // [T][ld] sparse part of thetabar (in: k+1, out: k)
   double* pend;                  // [Mtot][R] broadcast part of thetabar
   const int* col_meas;           // [T]
@@ -169,9 +170,7 @@ struct BwdArgs {
   const double* alpha;           // [Mtot]
   const double* Sd;              // [Mtot]
   const double* inv_S;           // [Mtot] 1 / S_m
-  const long long* col_off;      // [Mtot + 1] first column of each measure
   const double* a;               // [Mtot]
-  const float* irho;             // [Mtot] FP32 1/rho, as in the forward column step
   double* part;                  // [nchunks][1 + dim][R] chunk row sums of wbar, wbar zeta
   double* red;                   // [Mtot][1 + dim][R] chunk sums added per measure
   double* acc_prev;              // [Mtot][R] sum_s wbar_rs of the step after (k+1)
@@ -182,8 +181,7 @@ struct BwdArgs {
   double rho;
 };
 
-int bwd_max_rows();
-cudaError_t launch_bwd_step(int cost_dtype, int nchunks, cudaStream_t st, const BwdArgs& a);
+cudaError_t launch_bwd_step(int nchunks, cudaStream_t st, const BwdArgs& a);
 cudaError_t launch_bwd_theta0(long long T, cudaStream_t st, const BwdArgs& a);
 
 }  // namespace mam

@@ -329,6 +329,15 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
               atomicAdd(acc_m + 4 * idx + e,
                         (unsigned long long)f32_to_i64_rn(pv[e] * fx));
         }
+        if (A.amask) {  // active-set bits of this column (reverse sweep)
+          unsigned word = ((pv[0] > 0.f ? 1u : 0u) | (pv[1] > 0.f ? 2u : 0u) |
+                           (pv[2] > 0.f ? 4u : 0u) | (pv[3] > 0.f ? 8u : 0u))
+                          << (4 * (tid & 7));
+          word |= __shfl_xor_sync(0xffffffffu, word, 1);
+          word |= __shfl_xor_sync(0xffffffffu, word, 2);
+          word |= __shfl_xor_sync(0xffffffffu, word, 4);
+          if ((tid & 7) == 0 && 4 * idx < ld) A.amask[size_t(col) * A.mw + idx / 8] = word;
+        }
         if (idx < ld4) {
           const float4 ov = make_float4(lo(o01), hi(o01), lo(o23), hi(o23));
           if (DIAG) {

@@ -321,6 +321,15 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
               atomicAdd(acc_m + 4 * g + e,
                         (unsigned long long)f32_to_i64_rn(pv[e] * A.fx_scale));
         }
+        if (A.amask) {  // active-set bits of this column (reverse sweep)
+          unsigned word = ((pv[0] > 0.f ? 1u : 0u) | (pv[1] > 0.f ? 2u : 0u) |
+                           (pv[2] > 0.f ? 4u : 0u) | (pv[3] > 0.f ? 8u : 0u))
+                          << (4 * (lane & 7));
+          word |= __shfl_xor_sync(0xffffffffu, word, 1);
+          word |= __shfl_xor_sync(0xffffffffu, word, 2);
+          word |= __shfl_xor_sync(0xffffffffu, word, 4);
+          if ((lane & 7) == 0 && 4 * g < ld) A.amask[size_t(col) * A.mw + g / 8] = word;
+        }
         if (g < ld4) {
           if (DIAG) {
             const float4 c = CostIO<CT>::load4(cs, g);

@@ -126,9 +126,10 @@ def test_full_size_short_horizon(Mam):
         assert rel_l2(a, b) <= GRAD_TOL, rel_l2(a, b)
 
 
-def test_large_rows(Mam):
-    """R = 48 x 48 = 2304 takes the 512-thread reverse kernel."""
-    prob = config4(grid=48, M=2)
+@pytest.mark.parametrize("grid", [48, 66])
+def test_large_rows(Mam, grid):
+    """R = 2304 (ring forward kernel limit passed: CTA kernel) and R = 4356."""
+    prob = config4(grid=grid, M=2)
     K = 3
     p, gq, gz, gx = gpu_grads(Mam, prob, K, 2)
     _, oq, oz, ox = oracle_grads(prob, K)
