@@ -34,7 +34,8 @@ struct BackwardState {
   double* pend = nullptr;    // [Mtot][R]
   double* red = nullptr;     // [Mtot][1 + dim][R]
   double* acc_prev = nullptr;  // [Mtot][R]
-  double* part = nullptr;    // [nchunks][1 + dim][R]
+  float* part = nullptr;     // [nchunks][1 + dim][R]
+  float* pend_f = nullptr;   // [Mtot][R]
   long long* chunk_begin = nullptr;  // [nchunks + 1]
   int* meas_chunk = nullptr;         // [Mtot + 1]
   int nchunks = 0;
@@ -169,6 +170,7 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   cb.push_back(h->col_off[h->Mtot]);
   if (s == MAM_OK) s = balloc(h, b, &b->red, MR * (1 + dim), "adjoint row sums");
   if (s == MAM_OK) s = balloc(h, b, &b->acc_prev, MR, "adjoint row sums");
+  if (s == MAM_OK) s = balloc(h, b, &b->pend_f, MR, "adjoint marginals (fp32)");
   if (s == MAM_OK)
     s = balloc(h, b, &b->part, size_t(b->nchunks) * (1 + dim) * h->R, "adjoint chunk sums");
   if (s == MAM_OK) s = balloc(h, b, &b->chunk_begin, cb.size(), "chunk table");
@@ -231,6 +233,10 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   BWD_CUDA(cudaMemcpyAsync(b->pend, pend0.data(), sizeof(double) * MR, cudaMemcpyHostToDevice,
                            h->stream),
            "grad_p upload");
+  std::vector<float> pend0f(pend0.begin(), pend0.end());
+  BWD_CUDA(cudaMemcpyAsync(b->pend_f, pend0f.data(), sizeof(float) * MR, cudaMemcpyHostToDevice,
+                           h->stream),
+           "grad_p upload");
   BWD_CUDA(cudaMemsetAsync(b->stored, 0, sizeof(float) * Tl, h->stream), "memset");
   BWD_CUDA(cudaMemsetAsync(b->acc_prev, 0, sizeof(double) * MR, h->stream), "memset");
   BWD_CUDA(cudaMemsetAsync(b->qbar, 0, sizeof(double) * h->T, h->stream), "memset");
@@ -249,6 +255,7 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   A.inv_S = h->invS_d;
   A.a = h->a_d;
   A.part = b->part;
+  A.pend_f = b->pend_f;
   A.red = b->red;
   A.acc_prev = b->acc_prev;
   A.qbar = b->qbar;

@@ -30,8 +30,8 @@
 // part can be nonzero) has a bit.
 //
 // Layout of the work: a CTA owns a chunk of consecutive columns of one
-// measure, one warp per column (bwd_column_kernel); then a thread owns fixed
-// rows of the chunk and adds its columns in order (bwd_chunk_rowsum_kernel);
+// measure, one warp per column (bwd_column_kernel); then a thread owns one
+// row of a chunk and adds its columns in order (bwd_chunk_rowsum_kernel);
 // the chunks of a measure are added in a fixed order
 // (bwd_chunk_reduce_kernel).  No atomics, so the result does not depend on
 // scheduling.
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) bwd_column_kernel(const BwdArg
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long c0 = A.chunk_begin[blockIdx.x], c1 = A.chunk_begin[blockIdx.x + 1];
   const int m = A.col_meas[c0];
-  for (int i = tid; i < R; i += blockDim.x) pd_s[i] = float(A.pend[size_t(m) * R + i]);
+  for (int i = tid; i < R; i += blockDim.x) pd_s[i] = A.pend_f[size_t(m) * R + i];
   __syncthreads();
   const double coef = 2.0 * A.alpha[m] / A.rho;
   const unsigned bit = 1u << lane;
@@ -138,82 +138,134 @@ __global__ void __launch_bounds__(kBwdWarps * 32) bwd_column_kernel(const BwdArg
 
 // Per-row sums of one chunk's new stored part: part[chunk][0][r] = sum_s
 // wbar_rs, part[chunk][1 + k][r] = sum_s wbar_rs zeta_s[k], the columns added
-// in order.  A thread owns rows r = tid + i * blockDim.x; wbar is zero off the
+// in order.  Grid (chunk, row block): one thread per row; wbar is zero off the
 // step's active set, so only rows with a mask bit are read.
-__global__ void __launch_bounds__(256) bwd_chunk_rowsum_kernel(const BwdArgs A) {
-  const int tid = threadIdx.x;
+constexpr int kRsThreads = 128;
+__global__ void __launch_bounds__(kRsThreads) bwd_chunk_rowsum_kernel(const BwdArgs A) {
   const long long c0 = A.chunk_begin[blockIdx.x], c1 = A.chunk_begin[blockIdx.x + 1];
   const int R = A.R, ld = A.ld, dim = A.dim, mw = A.mw;
-  double* part = A.part + size_t(blockIdx.x) * (1 + dim) * R;
-  for (int r = tid; r < R; r += blockDim.x) {
-    const unsigned bit = 1u << (r & 31);
-    float sw = 0.f, sz[3] = {0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (long long col = c0; col < c1; ++col) {
-      if (A.am[size_t(col) * mw + (r >> 5)] & bit) {
-        const float wb = A.stored[size_t(col) * ld + r];
-        sw += wb;
+  const int r = blockIdx.y * kRsThreads + threadIdx.x;
+  if (r >= R) return;
+  const int nc = int(c1 - c0);  // <= kBwdChunk
+  const unsigned bit = 1u << (r & 31);
+  // the chunk's mask words of this row, loaded together
+  unsigned wd[kBwdChunk];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (k < dim) sz[k] = fmaf(wb, float(__ldg(A.zeta + size_t(col) * dim + k)), sz[k]);
-      }
+  for (int j = 0; j < kBwdChunk; ++j) wd[j] = j < nc ? A.am[size_t(c0 + j) * mw + (r >> 5)] : 0u;
+  float sw = 0.f, sz[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < kBwdChunk; ++j) {
+    if (wd[j] & bit) {
+      const long long col = c0 + j;
+      const float wb = A.stored[size_t(col) * ld + r];
+      sw += wb;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < dim) sz[k] = fmaf(wb, float(__ldg(A.zeta + size_t(col) * dim + k)), sz[k]);
     }
-    part[r] = double(sw);
-    for (int k = 0; k < dim; ++k) part[size_t(1 + k) * R + r] = double(sz[k]);
   }
+  float* part = A.part + size_t(blockIdx.x) * (1 + dim) * R;
+  part[r] = sw;
+  for (int k = 0; k < dim; ++k) part[size_t(1 + k) * R + r] = sz[k];
 }
 
 // Sums the chunk partials of each measure in a fixed order:
 // red[m][k][r] = sum over the chunks j of measure m of part[j][k][r]
-// (k = 0: sum_s wbar_rs, k = 1..dim: sum_s wbar_rs zeta_s).  Block
-// (kRedRows rows) x (kRedSlices chunk slices), grid (rows, measures, 1 + dim).
+// (k = 0: sum_s wbar_rs, k = 1..dim: sum_s wbar_rs zeta_s).  Compensated
+// FP32 summation (Knuth's TwoSum: the rounding error of every addition is
+// carried in a second float), so the result keeps about twice the FP32
+// precision without FP64 arithmetic.  Block (kRedRows rows) x (kRedSlices
+// chunk slices), grid (rows, measures, 1 + dim).
+__device__ __forceinline__ void two_sum(float& s, float& c, float x) {
+  const float t = s + x;
+  const float z = t - s;
+  c += (s - (t - z)) + (x - z);
+  s = t;
+}
+
 constexpr int kRedRows = 32, kRedSlices = 8;
 __global__ void __launch_bounds__(kRedRows * kRedSlices) bwd_chunk_reduce_kernel(const BwdArgs A) {
-  __shared__ double sh[kRedSlices][kRedRows];
+  __shared__ float sh[2][kRedSlices][kRedRows];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = blockIdx.x * kRedRows + tx;
   const int m = blockIdx.y, k = blockIdx.z;
   const int K1 = 1 + A.dim, R = A.R;
-  double s = 0.0;
+  float s = 0.f, c = 0.f;
   if (r < R) {
 #pragma unroll 4
     for (int j = A.meas_chunk[m] + ty; j < A.meas_chunk[m + 1]; j += kRedSlices)
-      s += A.part[(size_t(j) * K1 + k) * R + r];
+      two_sum(s, c, A.part[(size_t(j) * K1 + k) * R + r]);
   }
-  sh[ty][tx] = s;
+  sh[0][ty][tx] = s;
+  sh[1][ty][tx] = c;
   __syncthreads();
   if (ty == 0 && r < R) {
-    double t = 0.0;
+    float t = 0.f, ct = 0.f;
 #pragma unroll
-    for (int y = 0; y < kRedSlices; ++y) t += sh[y][tx];
-    A.red[(size_t(m) * K1 + k) * R + r] = t;
+    for (int y = 0; y < kRedSlices; ++y) {
+      two_sum(t, ct, sh[0][y][tx]);
+      ct += sh[1][y][tx];
+    }
+    A.red[(size_t(m) * K1 + k) * R + r] = double(t) + double(ct);
   }
 }
 
 // Per row r: dbar, pbar, the new broadcast part of thetabar and xibar.
 // acc_prev holds sum_s wbar^(k+1)_rs (the stored part entering this step).
-__global__ void bwd_row_kernel(const BwdArgs A) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= A.R) return;
+// Block (kRowRows rows) x (kRowSlices measure slices): a thread takes the
+// measures m = y, y + kRowSlices, ... of its row (at most kRowKeep of them
+// kept in registers between the two phases); pbar and the xibar terms are
+// added over the slices in shared memory in a fixed order.
+constexpr int kRowRows = 32, kRowSlices = 8, kRowKeep = 8;
+__global__ void __launch_bounds__(kRowRows * kRowSlices) bwd_row_kernel(const BwdArgs A) {
+  __shared__ double sp[kRowSlices][kRowRows];
+  __shared__ double sx[3][kRowSlices][kRowRows];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r = blockIdx.x * kRowRows + tx;
+  const bool row = r < A.R;
   const int dim = A.dim, R = A.R, K1 = 1 + dim;
-  double pbar = 0.0;
-  for (int m = 0; m < A.Mtot; ++m) {
-    const size_t o = size_t(m) * R + r;
-    const double w = A.red[size_t(m) * K1 * R + r];
-    const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
-    pbar += dbar * A.inv_S[m];
-  }
-  for (int m = 0; m < A.Mtot; ++m) {
-    const size_t o = size_t(m) * R + r;
-    const double w = A.red[size_t(m) * K1 * R + r];
-    const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
-    const double coef = 2.0 * A.alpha[m] / A.rho;
-    for (int k = 0; k < dim; ++k) {
-      const double wz = A.red[(size_t(m) * K1 + 1 + k) * R + r];
-      A.xibar[size_t(r) * dim + k] -= coef * (A.xi[size_t(r) * dim + k] * w - wz);
+  double pb = 0.0, xs[3] = {0.0, 0.0, 0.0};
+  double dkeep[kRowKeep];
+  double xr[3] = {0.0, 0.0, 0.0};
+  if (row)
+    for (int k = 0; k < dim; ++k) xr[k] = A.xi[size_t(r) * dim + k];
+  int q = 0;
+  if (row) {
+    for (int m = ty; m < A.Mtot; m += kRowSlices, ++q) {
+      const size_t o = size_t(m) * R + r;
+      const double w = A.red[size_t(m) * K1 * R + r];
+      const double dbar = 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
+      if (q < kRowKeep) dkeep[q] = dbar;
+      pb += dbar * A.inv_S[m];
+      const double coef = 2.0 * A.alpha[m] / A.rho;
+      for (int k = 0; k < dim; ++k)
+        xs[k] += coef * (xr[k] * w - A.red[(size_t(m) * K1 + 1 + k) * R + r]);
     }
-    A.pend[o] = -dbar * A.inv_S[m] + A.a[m] * pbar;
-    A.acc_prev[o] = w;
+  }
+  sp[ty][tx] = pb;
+  for (int k = 0; k < 3; ++k) sx[k][ty][tx] = xs[k];
+  __syncthreads();
+  double pbar = 0.0;
+#pragma unroll
+  for (int y = 0; y < kRowSlices; ++y) pbar += sp[y][tx];
+  if (row && ty == 0)
+    for (int k = 0; k < dim; ++k) {
+      double t = 0.0;
+      for (int y = 0; y < kRowSlices; ++y) t += sx[k][y][tx];
+      A.xibar[size_t(r) * dim + k] -= t;
+    }
+  if (row) {
+    q = 0;
+    for (int m = ty; m < A.Mtot; m += kRowSlices, ++q) {
+      const size_t o = size_t(m) * R + r;
+      const double w = A.red[size_t(m) * K1 * R + r];
+      const double dbar = q < kRowKeep ? dkeep[q]
+                                       : 2.0 * w - (A.acc_prev[o] + A.Sd[m] * A.pend[o]);
+      const double pn = -dbar * A.inv_S[m] + A.a[m] * pbar;
+      A.pend[o] = pn;
+      A.pend_f[o] = float(pn);
+      A.acc_prev[o] = w;
+    }
   }
 }
 
@@ -235,12 +287,13 @@ cudaError_t launch_bwd_step(int nchunks, cudaStream_t st, const BwdArgs& a) {
   bwd_column_kernel<<<nchunks, kBwdWarps * 32, sizeof(float) * size_t(a.R), st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  bwd_chunk_rowsum_kernel<<<nchunks, 256, 0, st>>>(a);
+  bwd_chunk_rowsum_kernel<<<dim3(nchunks, (a.R + kRsThreads - 1) / kRsThreads), kRsThreads, 0,
+                            st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bwd_chunk_reduce_kernel<<<dim3((a.R + kRedRows - 1) / kRedRows, a.Mtot, 1 + a.dim),
                             dim3(kRedRows, kRedSlices), 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bwd_row_kernel<<<(a.R + 63) / 64, 64, 0, st>>>(a);
+  bwd_row_kernel<<<(a.R + kRowRows - 1) / kRowRows, dim3(kRowRows, kRowSlices), 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -171,7 +171,8 @@ struct BwdArgs {
   const double* Sd;              // [Mtot]
   const double* inv_S;           // [Mtot] 1 / S_m
   const double* a;               // [Mtot]
-  double* part;                  // [nchunks][1 + dim][R] chunk row sums of wbar, wbar zeta
+  float* part;                   // [nchunks][1 + dim][R] chunk row sums of wbar, wbar zeta
+  float* pend_f;                 // [Mtot][R] FP32 copy of pend for the column step
   double* red;                   // [Mtot][1 + dim][R] chunk sums added per measure
   double* acc_prev;              // [Mtot][R] sum_s wbar_rs of the step after (k+1)
   double* qbar;                  // [T]
