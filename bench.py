@@ -312,6 +312,7 @@ def run_reference(args):
     sample_entries = len(idx) * prob.R
     value = args.steps * sample_entries / dt
     cfg = describe(args.workload, probs, "f64", T, entries)
+    cfg["theta_dtype"] = "f64"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
