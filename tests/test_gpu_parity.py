@@ -252,6 +252,24 @@ def test_batched_matches_separate_problems(Mam):
         assert abs(objs[i]["w_hat"] - ref["w_hat"]) <= 1e-4 * ref["w_hat"]
 
 
+@pytest.mark.parametrize("n, M, K", [(320, 3, 3), (160, 20, 8)])
+def test_batched_averaging_block_shapes(Mam, n, M, K):
+    """Batches shaped so that the averaging kernel runs with 1 measure slice
+    (320 problems of 3 measures, R = 9) and with 4 slices (160 problems of 20
+    measures, R = 64); sampled problems follow the oracle."""
+    probs = [tiny_problem(5000 + i, M=M, K=K, rho=6.0) for i in range(n)]
+    iters = 15
+    with Mam(problems=probs, diag="never") as batch:
+        batch.step(iters)
+        pb = batch.barycenter()
+    for i in (0, n // 2, n - 1):
+        prep = prepare(probs[i])
+        orc = MamOracle(prep, probs[i].rho)
+        orc.run(iters)
+        Q, Qa = masses(prep)
+        assert np.abs(pb[i] - orc.barycenter()).sum() / Qa <= ITER_TOL
+
+
 def test_solve_reaches_gap(Mam):
     prob = tiny_problem(12, M=3, K=4, rho=5.0)
     with Mam(prob) as gpu:
