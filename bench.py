@@ -317,7 +317,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded images, see DESIGN.md)", "config": cfg,
+            "data": "synthetic (seeded images shaped like the paper's workloads)", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(idx)} columns x R={prob.R} of the workload per "
                                        f"step (numpy FP64 oracle, single thread)"},
@@ -439,7 +439,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded images standing in for the "
-                                    "paper's datasets; see DESIGN.md)",
+                                    "paper's datasets)",
             "config": cfg, "roofline": roof, "gpu_launches": 2 * args.steps,
             "clocks": clocks}
 

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (the ones the method's use fixes):
+Tolerances (fixed by how the method is used):
 * iterates, first 50 iterations: ||theta_gpu - theta_ref||_1 / sum_m Q_m and
   ||p_gpu - p_ref||_1 / sum_m a_m Q_m below 1e-5;
 * objective after the full run: |W_gpu - W_ref| / |W_ref| below 1e-4.
