@@ -415,7 +415,7 @@ __device__ __forceinline__ long long mul_q62(long long x, long long a) {
   return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
 }
 
-template <int SL>
+template <int SL, bool DIAG>
 __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
   constexpr int RX = kAvgThreads / SL;
   constexpr int NW = kAvgThreads / 32;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
   if (flat == 0) t_sh = float(A.t_used[pr]);
   const Sched sc = A.sched[draw_index_set(A.draw, *A.iter - 1)];
   const bool row = r < A.R;
-  const bool diag = A.diag != 0;
+  constexpr bool diag = DIAG;  // compile-time: no FP64 per (m, r) without diagnostics
   __syncthreads();
   const float t_old = t_sh;
   // pass 1: new marginals of this slice's measures, partial sums of a_m p^(m).
@@ -828,12 +828,23 @@ cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
 }
 
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st) {
+  const dim3 grid(nblk, a.P);
+  const bool dg = a.diag != 0;
   switch (a.slices) {
-    case 1: return launch_pdl(average_kernel<1>, dim3(nblk, a.P), dim3(kAvgThreads, 1), 0, st, a);
-    case 2: return launch_pdl(average_kernel<2>, dim3(nblk, a.P), dim3(kAvgThreads / 2, 2), 0, st, a);
-    case 4: return launch_pdl(average_kernel<4>, dim3(nblk, a.P), dim3(kAvgThreads / 4, 4), 0, st, a);
-    case 8: return launch_pdl(average_kernel<8>, dim3(nblk, a.P), dim3(kAvgThreads / 8, 8), 0, st, a);
-    default: return cudaErrorInvalidValue;
+    case 1:
+      return dg ? launch_pdl(average_kernel<1, true>, grid, dim3(kAvgThreads, 1), 0, st, a)
+                : launch_pdl(average_kernel<1, false>, grid, dim3(kAvgThreads, 1), 0, st, a);
+    case 2:
+      return dg ? launch_pdl(average_kernel<2, true>, grid, dim3(kAvgThreads / 2, 2), 0, st, a)
+                : launch_pdl(average_kernel<2, false>, grid, dim3(kAvgThreads / 2, 2), 0, st, a);
+    case 4:
+      return dg ? launch_pdl(average_kernel<4, true>, grid, dim3(kAvgThreads / 4, 4), 0, st, a)
+                : launch_pdl(average_kernel<4, false>, grid, dim3(kAvgThreads / 4, 4), 0, st, a);
+    case 8:
+      return dg ? launch_pdl(average_kernel<8, true>, grid, dim3(kAvgThreads / 8, 8), 0, st, a)
+                : launch_pdl(average_kernel<8, false>, grid, dim3(kAvgThreads / 8, 8), 0, st, a);
+    default:
+      return cudaErrorInvalidValue;
   }
 }
 
