@@ -1,5 +1,5 @@
-"""torch.autograd binding of the unrolled MAM barycenter (argument marshalling
-only).
+"""torch binding of libmam (argument marshalling only): ``solve`` and the
+unrolled barycenter as a ``torch.autograd.Function``.
 
 ``MamFunction.apply(q, zeta, xi, S, alpha, rho, K, ckpt_every, theta0)``
 returns p^K, the barycenter estimate after K iterations of Algorithm 1 from
@@ -68,3 +68,21 @@ def unrolled_barycenter(q, zeta, xi, S, alpha, rho=100.0, K=200, ckpt_every=20,
     """Functional form of ``MamFunction.apply``."""
     return MamFunction.apply(q, zeta, xi, list(S), list(alpha), rho, K, ckpt_every,
                              theta0)
+
+
+def solve(q, zeta, xi, S, alpha, rho=100.0, gamma=math.inf, max_iters=20000, gap_tol=1e-4,
+          check_every=10, cost_dtype="f32", n_bundles=1, seed=0):
+    """MAM to a relative gap of gap_tol (mam_solve) on torch's current CUDA
+    stream; returns (p, info).  p is a float64 tensor [R] on the device of q
+    (copied device to device from the library), info has the iterations run,
+    the last gap and the diagnostics of mam_objective."""
+    prob = _problem(q, zeta, xi, S, alpha, rho)
+    prob.gamma = float(gamma)
+    prob.n_bundles = int(n_bundles)
+    stream = torch.cuda.current_stream(q.device if q.is_cuda else None)
+    with Mam(prob, cost_dtype=cost_dtype, diag="never", seed=seed, stream=stream) as g:
+        iters, gap = g.solve(int(max_iters), float(gap_tol), 0.0, int(check_every))
+        info = dict(g.objective(), iterations=iters, gap=gap)
+        dev = q.device if q.is_cuda else torch.device("cuda")
+        p = g.barycenter_into(torch.empty(g.R, dtype=torch.float64, device=dev))
+    return p.to(q.device), info

@@ -187,3 +187,21 @@ def test_torch_autograd_function(Mam):
     assert rel_l2(q.grad.cpu().numpy(), oq) <= GRAD_TOL
     assert rel_l2(zeta.grad.cpu().numpy(), oz) <= GRAD_TOL
     assert rel_l2(xi.grad.cpu().numpy(), ox) <= GRAD_TOL
+
+
+def test_torch_solve(Mam):
+    """torch_api.solve: tensors in, the barycenter tensor out, on torch's stream."""
+    torch = pytest.importorskip("torch")
+    from paper_2309_05315_gb300.torch_api import solve
+    prob = config4(grid=16, M=3)
+    S = [len(q) for q in prob.q]
+    q = torch.tensor(np.concatenate(prob.q), device="cuda")
+    zeta = torch.tensor(np.concatenate(prob.zeta), device="cuda")
+    xi = torch.tensor(prob.xi, device="cuda")
+    p, info = solve(q, zeta, xi, S, prob.alpha, prob.rho, max_iters=20000, gap_tol=1e-4)
+    assert p.is_cuda and p.dtype == torch.float64 and p.shape == (prob.R,)
+    assert info["gap"] <= 1e-4
+    with Mam(prob, diag="never") as g:
+        it, gap = g.solve(20000, 1e-4, 0.0, 10)
+        np.testing.assert_array_equal(p.cpu().numpy(), g.barycenter())
+        assert it == info["iterations"]
