@@ -198,9 +198,10 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
                         double* grad_zeta, double* grad_xi);
 
 /* Kernel configuration of the column step.
- * kind 0: one CTA per column.  threads (multiple of 32, <= 1024) x vec
- *   (1..6 or 8) float4 groups cover the column; stages (2..4) is the depth
- *   of the bulk-copy pipeline.  Any R up to 12288.
+ * kind 0: one CTA per column.  threads (multiple of 32, up to 1024 for vec
+ *   1, 768 for 2, 512 for 3..4, 192 for 5..6, 384 for 8) x vec float4
+ *   groups cover the column; stages (1..4) is the depth of the bulk-copy
+ *   pipeline.  Any R up to 12288.
  * kind 1: one warp per column.  vec (1,2,4,7,8,13,16) float4 groups
  *   per lane cover the column (R up to 2048); stages (>= threads/32) is the
  *   number of shared-memory ring slots; threads/32 warps per CTA.

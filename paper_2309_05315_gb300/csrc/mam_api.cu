@@ -176,7 +176,7 @@ size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c) {
   const size_t tile = size_t(c.threads) * c.vec * 4;
   return size_t(c.stages) * tile * (sizeof(float) + cost_elem_size(h->cost_dtype)) +
          4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4) +
-         kRedSlots * sizeof(double);
+         kRedSlots * sizeof(double) + tile * sizeof(float);
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
@@ -216,9 +216,9 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
                 "threads * vec * 4 must cover the padded column (" +
                     std::to_string(h->ld) + ")");
-  if (c.stages < 2 || c.stages > 4)
+  if (c.stages < 1 || c.stages > 4)
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
-                "stages must be 0 (one warp per column) or 2..4");
+                "stages must be 1..4");
   if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32)
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "ctas_per_sm must be 0..32");
   if (c.bisect_depth < 0 || c.bisect_depth > 30)
@@ -271,10 +271,31 @@ mam_kernel_config default_config(const mam_problem* h) {
       best.vec = nv;
     }
   }
-  best.stages = 2;
   best.ctas_per_sm = 0;
   best.bisect_depth = 4;
   best.kind = 0;
+  // Two stages overlap the next column's copy with this one's search; one
+  // stage frees the shared memory for more resident CTAs, whose columns hide
+  // the copy instead (measured at R = 3600, 160 x 6: 54 us per step with one
+  // stage at 4 CTAs/SM, 60-64 us with two at 2 CTAs/SM).  Take one stage
+  // when it admits more CTAs per SM.
+  int occ_by_stages[3] = {0, 0, 0};
+  for (int st = 1; st <= 2; ++st) {
+    best.stages = st;
+    const size_t smem = column_smem_bytes(h, best);
+    int occ = 1 << 30;
+    for (int dg = 0; dg < 2; ++dg) {
+      int o = 0;
+      if (smem > 232448 ||
+          set_column_smem(best.vec, h->cost_dtype, dg != 0, smem) != cudaSuccess ||
+          column_occupancy(best.vec, h->cost_dtype, dg != 0, best.threads, smem, &o) !=
+              cudaSuccess)
+        o = 0;
+      occ = std::min(occ, o);
+    }
+    occ_by_stages[st] = occ;
+  }
+  best.stages = occ_by_stages[1] > occ_by_stages[2] ? 1 : 2;
   return best;
 }
 

@@ -336,7 +336,7 @@ mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best) 
     for (int extra = 0; extra < 2; ++extra) {
       const int t = nt + 32 * extra;
       if (t > column_max_threads(nv)) continue;
-      for (int stg = 2; stg <= 3; ++stg)
+      for (int stg = 1; stg <= 3; ++stg)
         for (int cps : {0, 1, 2}) {
           mam_kernel_config c{t, nv, stg, cps, start.bisect_depth, 0};
           if (check_config(h, c) == MAM_OK) cands.push_back(c);

@@ -176,7 +176,17 @@ __device__ __forceinline__ bool newton_certified(float gap0, float dl, float l0)
 template <int NV>
 struct MaxThreads {
   static constexpr int value = NV == 1 ? 1024 : NV == 2 ? 768
-                               : NV <= 6 ? 512 : 384;
+                               : NV <= 4 ? 512 : NV <= 6 ? 192 : 384;
+};
+// Resident CTAs per SM the register allocation is sized for.  The 5- and
+// 6-group shapes (columns of up to 3840 / 4608 rows) are held to 4 CTAs of
+// 192 threads, the 8-group shape (up to 12288 rows) to 2 CTAs of 384: with
+// the shift d in shared memory this spills at most a few bytes, and
+// with a one-stage pipeline the extra resident columns hide the copies
+// (R = 3600: 54 vs 56 us per step; R = 10000 unbalanced: 0.69 vs 0.82 ms).
+template <int NV>
+struct MinCtas {
+  static constexpr int value = (NV == 5 || NV == 6) ? 4 : NV == 8 ? 2 : 1;
 };
 
 // ------------------------------------------------------------ helpers

@@ -27,8 +27,8 @@ namespace {
 // Step 2 of Algorithm 1 for one CTA's slice of the index set, one column at
 // a time.  Thread `tid` owns the float4 groups idx = v*nt + tid (v < NV) of
 // every column, i.e. rows r = 4*idx .. 4*idx+3, held as two FP32 pairs; its
-// shift d^(m)_r stays in registers while consecutive columns belong to the
-// same measure.
+// shift d^(m)_r is written once per measure to a thread-private shared-memory
+// tile and read from there by every column of that measure.
 //
 // Per column s of measure m (tau = q_s):
 //   w_r     = theta_rs + 2 d_r - c_rs / rho        (Alg. 1, w)
@@ -57,7 +57,7 @@ namespace {
 // once per CTA), and the cost's padding rows R..ld-1 are +inf in memory, so
 // every such row has w = -inf and never enters the active set.
 template <int NV, typename CT, bool DIAG>
-__global__ void __launch_bounds__(MaxThreads<NV>::value)
+__global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
     column_kernel(const ColArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x;
@@ -77,6 +77,10 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
       smem + size_t(stages) * tile * (sizeof(float) + sizeof(CT)));
   float4* red = reinterpret_cast<float4*>(bar + 4);
   double* dred = reinterpret_cast<double*>(red + 2 * kRedSlots);
+  // d of this thread's rows for the current measure: thread-private (a thread
+  // reads only the rows it wrote), so it needs no barrier, and it frees the
+  // registers that would hold it across the column loop.
+  float4* d_s = reinterpret_cast<float4*>(dred + kRedSlots);
 
   const long long k_iter = *A.iter;
   const Sched sc = A.sched[draw_index_set(A.draw, k_iter)];
@@ -126,7 +130,6 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
       }
     };
 
-    f2_t d2[NV][2];  // d for rows 4*idx + (0,1) and (2,3)
     float rho_m = 0.f;
     f2_t nirho2 = 0ull;
     const f2_t two2 = pk(2.f, 2.f);
@@ -177,8 +180,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
             const int r = 4 * idx + e;
             dv[e] = r < R ? __fmul_rn(tf, dl[r]) : 0.f;
           }
-          d2[v][0] = pk(dv[0], dv[1]);
-          d2[v][1] = pk(dv[2], dv[3]);
+          d_s[idx] = make_float4(dv[0], dv[1], dv[2], dv[3]);
         }
       }
       const int s = int(j % stages);
@@ -203,16 +205,18 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         const float4 th = reinterpret_cast<const float4*>(ths)[idx];
         const float4 c = CostIO<CT>::load4(cs, idx);
         const f2_t c01 = pk(c.x, c.y), c23 = pk(c.z, c.w);
-        w2[v][0] = fma2(c01, nirho2, fma2(two2, d2[v][0], pk(th.x, th.y)));
-        w2[v][1] = fma2(c23, nirho2, fma2(two2, d2[v][1], pk(th.z, th.w)));
+        const float4 dd = d_s[idx];
+        const f2_t d01 = pk(dd.x, dd.y), d23 = pk(dd.z, dd.w);
+        w2[v][0] = fma2(c01, nirho2, fma2(two2, d01, pk(th.x, th.y)));
+        w2[v][1] = fma2(c23, nirho2, fma2(two2, d23, pk(th.z, th.w)));
         const f2_t x0 = sub2(w2[v][0], l02), x1 = sub2(w2[v][1], l02);
         gap0 = fminf(gap0, fminf(fminf(fabsf(lo(x0)), fabsf(hi(x0))),
                                  fminf(fabsf(lo(x1)), fabsf(hi(x1)))));
         fa = add2(fa, relu2(x0, n));
         fb = add2(fb, relu2(x1, n));
         if (DIAG) {
-          lbmin = fminf(lbmin, fminf(fminf(c.x - rho_m * lo(d2[v][0]), c.y - rho_m * hi(d2[v][0])),
-                                     fminf(c.z - rho_m * lo(d2[v][1]), c.w - rho_m * hi(d2[v][1]))));
+          lbmin = fminf(lbmin, fminf(fminf(c.x - rho_m * dd.x, c.y - rho_m * dd.y),
+                                     fminf(c.z - rho_m * dd.z, c.w - rho_m * dd.w)));
         }
       }
       // The failure flag rides in the first reduction (f < 0 marks it).
@@ -316,8 +320,9 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value)
         float dummy = 0.f;
         const f2_t p01 = relu2(sub2(w2[v][0], lf2), dummy);
         const f2_t p23 = relu2(sub2(w2[v][1], lf2), dummy);
-        const f2_t o01 = sub2(p01, d2[v][0]);
-        const f2_t o23 = sub2(p23, d2[v][1]);
+        const float4 dd = d_s[idx];
+        const f2_t o01 = sub2(p01, pk(dd.x, dd.y));
+        const f2_t o23 = sub2(p23, pk(dd.z, dd.w));
         const float pv[4] = {lo(p01), hi(p01), lo(p23), hi(p23)};
         // pihat is sparse: convert and add only where some lane of the warp
         // has an active row in this group.
