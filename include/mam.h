@@ -203,8 +203,9 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
  *   groups cover the column; stages (1..4) is the depth of the bulk-copy
  *   pipeline.  Any R up to 12288.
  * kind 1: one warp per column.  vec (1,2,4,7,8,13,16) float4 groups
- *   per lane cover the column (R up to 2048); stages (>= threads/32) is the
- *   number of shared-memory ring slots; threads/32 warps per CTA.
+ *   per lane cover the column (R up to 2048; the default for R up to
+ *   1024); stages (>= threads/32) is the number of shared-memory ring
+ *   slots; threads/32 warps per CTA.
  * ctas_per_sm: 0 = occupancy maximum.  bisect_depth (0..30): bisection steps
  * on a cold start.  Invalid combinations return MAM_ERR_INVALID_ARG. */
 typedef struct {

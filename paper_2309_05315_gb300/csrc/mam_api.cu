@@ -229,13 +229,14 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
   return MAM_OK;
 }
 
-// Default launch shape.  Columns of up to 2048 rows go to the
-// warp-per-column ring kernel (measured: 51 us vs 98 us per column step at
-// R = 1600, 0.72 ms vs 1.86 ms at R = 784 x 256 problems); longer columns to
-// the one-CTA-per-column kernel (62 us vs 81 us at R = 3600).
+// Default launch shape.  Columns of up to 1024 rows go to the
+// warp-per-column ring kernel (measured at R = 784 x 256 problems: 0.84 ms
+// per step against 0.96 ms for the best CTA shape); longer columns to the
+// one-CTA-per-column kernel (R = 1600: 49 us per step with 96 x 5, 52 us
+// for the ring kernel; R = 3600: 54 us against 81 us).
 mam_kernel_config default_config(const mam_problem* h) {
   const int ld4 = h->ld / 4;
-  if (h->ld <= 2048) {
+  if (h->ld <= 1024) {
     // The narrowest compiled width that covers the column, up to 12 ring
     // slots (as many as fit in shared memory) and one warp per slot.
     const int need = (ld4 + 31) / 32;
@@ -263,8 +264,10 @@ mam_kernel_config default_config(const mam_problem* h) {
     if (nt > column_max_threads(nv)) continue;
     const double util = double(ld4) / (double(nt) * nv);
     // Prefer covering the column with few warps: every threshold-search pass
-    // ends in a CTA-wide reduction whose latency grows with the warp count.
-    const double score = util - 0.01 * (nt / 32);
+    // ends in a CTA-wide reduction whose latency grows with the warp count
+    // (R = 1600, one stage: 48-51 us per step with 3 warps x 5 groups,
+    // 51-54 with 4 x 4, 57-62 with 5 x 3, 59-62 with 7 x 2).
+    const double score = util - 0.03 * (nt / 32);
     if (score > best_score + 1e-12) {
       best_score = score;
       best.threads = nt;

@@ -186,6 +186,19 @@ def test_ring_slots_on_stroke_images(Mam, cfg):
     compare_trajectory(Mam, prob, 30, cost_dtype="bf16", oracle_cost="bf16", config=cfg)
 
 
+@pytest.mark.parametrize("cfg", [
+    None,  # the default: one CTA per column, 96 threads x 5 groups, one stage
+    dict(kind=1, threads=384, vec=13, stages=12, ctas_per_sm=2),
+    dict(kind=1, threads=128, vec=16, stages=4, ctas_per_sm=2),
+    dict(kind=0, threads=128, vec=4, stages=2, ctas_per_sm=0),
+])
+def test_mixture_R1600_kernels(Mam, cfg):
+    """The 40x40 Gaussian-mixture workload (R = 1600, 8 measures): the default
+    CTA shape and the warp-per-column ring kernel at its two widest widths."""
+    from workloads import config4
+    compare_trajectory(Mam, config4(), 3, config=cfg)
+
+
 def test_cold_start_bisection_depths(Mam):
     for kind, extra in ((1, {}), (0, dict(threads=64, vec=1, stages=2))):
         for depth in (0, 12, 30):
