@@ -226,8 +226,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
       fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](long long j) {  // one thread
-      const int s = int(j % K);
+    auto issue = [&](int j, int s) {  // column j into slot s = j mod K; one thread
       const long long col = c0 + j;
       mbar_expect_tx(&full[s], bytes_th + bytes_c);
       bulk_load(th_s + size_t(s) * kSlot, A.theta + size_t(col) * ld, bytes_th, &full[s]);
@@ -237,7 +236,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
       atomicAdd(&issued_cnt[s], 1);
     };
     if (tid == 0)
-      for (long long j = 0; j < ncol && j < K; ++j) issue(j);
+      for (int j = 0; j < ncol && j < K; ++j) issue(j, j);
 
     pdl_wait();  // the averaging kernel's outputs are used from here on
     int p_cur = -1;
@@ -247,13 +246,14 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
     while (true) {
       int jj = 0;
       if (lane == 0) jj = atomicAdd(next, 1);
-      const long long j = __shfl_sync(0xffffffffu, jj, 0);
+      const int j = __shfl_sync(0xffffffffu, jj, 0);
       if (j >= ncol) break;
-      const int s = int(j % K);
+      const int jq = j / K;  // 32-bit: a CTA holds fewer than 2^31 columns
+      const int s = j - jq * K;
       bool ok = true;
-      if (lane == 0) ok = wait_count_bounded(&issued_cnt[s], int(j / K) + 1, kWaitLimitNs);
+      if (lane == 0) ok = wait_count_bounded(&issued_cnt[s], jq + 1, kWaitLimitNs);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (ok) ok = mbar_wait_bounded(&full[s], uint32_t((j / K) & 1), kWaitLimitNs);
+      if (ok) ok = mbar_wait_bounded(&full[s], uint32_t(jq & 1), kWaitLimitNs);
       if (!__all_sync(0xffffffffu, ok)) {
         failed = true;
         break;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
       }
       if (!DIAG) {
         __syncwarp();  // every lane has read the slot
-        if (lane == 0 && j + K < ncol) issue(j + K);
+        if (lane == 0 && j + K < ncol) issue(j + K, s);
       }
       int np = 0;
       const float lam = warp_search<NV>(w, tau, lam_prev, A.bisect_depth, np);
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
           A.diag_lb[col] = tau * lbmin;
         }
         __syncwarp();
-        if (lane == 0 && j + K < ncol) issue(j + K);
+        if (lane == 0 && j + K < ncol) issue(j + K, s);
       }
       if (lane == 0) A.lam[col] = lam;
     }
