@@ -95,17 +95,26 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+# Sources of each column-step kernel: a recorded traffic figure holds only
+# while the hash of its kernel's sources is unchanged.
+KERNEL_SOURCES = {
+    "column_kernel": ("mam_kernels.cu", "mam_device.cuh", "mam_internal.h"),
+    "column_ring_kernel": ("mam_warp_kernel.cu", "mam_device.cuh", "mam_internal.h"),
+}
+
+
+def kernel_source_hash(kernel="column_kernel"):
     h = hashlib.sha256()
-    for f in ("mam_kernels.cu", "mam_device.cuh", "mam_internal.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2309_05315_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_name, entries):
-    """DRAM bytes per column-kernel launch from the committed ncu summary,
-    scaled to this launch by plan entries; None if the kernel changed."""
+def ncu_traffic(workload_name, entries, kernel="column_kernel"):
+    """DRAM bytes per column-step launch from the committed ncu summary,
+    scaled to this launch by plan entries; None if there is no record for
+    this workload and kernel, or the kernel's sources changed since."""
     path = os.path.join(ROOT, "profiles", "column_kernel_traffic.json")
     try:
         with open(path) as f:
@@ -113,7 +122,8 @@ def ncu_traffic(workload_name, entries):
     except Exception:
         return None
     rec = d.get(workload_name)
-    if not rec or rec.get("kernel_sha") != kernel_source_hash():
+    if (not rec or rec.get("kernel", "column_kernel") != kernel
+            or rec.get("kernel_sha") != kernel_source_hash(kernel)):
         return None
     return float(rec["dram_bytes_per_entry"]) * entries
 
@@ -424,10 +434,11 @@ def main():
     cfg["l2"] = (f"inputs larger than L2: {alg_bytes / 1e6:.0f} MB of plan/cost traffic per "
                  "step, no flush")
     cfg["kernel_config"] = gpu.config()
-    traffic = ncu_traffic(cfg["workload"], entries_per_step)
+    kernel = "column_ring_kernel" if cfg["kernel_config"]["kind"] == 1 else "column_kernel"
+    traffic = ncu_traffic(cfg["workload"], entries_per_step, kernel)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "column_kernel", "peak_kind": f"{peak_kind} copy bandwidth",
+            "kernel": kernel, "peak_kind": f"{peak_kind} copy bandwidth",
             "algorithmic_bytes_per_launch": alg_bytes,
             "duration_window": f"{n_timed} launches, one event pair each, after the timed region",
             "step_achieved_gbs": alg_bytes / (ms / args.steps / 1e3) / 1e9,
