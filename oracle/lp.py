@@ -9,6 +9,11 @@ barycenter p.  Rows:
 p is left free: pi >= 0 already makes it nonnegative and the column rows fix
 its mass.  The duals (u, v) of the two row families satisfy
 c^(m)_{rs} - u^(m)_s - v^(m)_r >= 0 and sum_m v^(m) = 0.
+
+With ``capped=True`` the column rows become sum_r pi^(m)_{rs} <= q^(m)_s:
+the full unbalanced extension with g the indicator of L (every plan has the
+same row marginals), whose shifted cost alpha_m (d - eta) comes with the
+prepared data.
 """
 from __future__ import annotations
 
@@ -16,7 +21,7 @@ import numpy as np
 from scipy import optimize, sparse
 
 
-def solve_barycenter_lp(prep):
+def solve_barycenter_lp(prep, capped: bool = False):
     """Return dict(opt, pi (list of (S_m,R)), p, u (list), v (list))."""
     M, R = prep.M, prep.R
     S = [int(s) for s in prep.S]
@@ -42,12 +47,18 @@ def solve_barycenter_lp(prep):
     A = sparse.csr_matrix((vals, (rows, cols)), shape=(row, nvar))
     cvec = np.concatenate([prep.c[m].ravel() for m in range(M)] + [np.zeros(R)])
     bounds = [(0, None)] * (nvar - R) + [(None, None)] * R
-    res = optimize.linprog(cvec, A_eq=A, b_eq=np.asarray(b), bounds=bounds,
-                           method="highs")
+    b = np.asarray(b)
+    if capped:
+        ncol = sum(S)  # the column rows come first
+        res = optimize.linprog(cvec, A_ub=A[:ncol], b_ub=b[:ncol], A_eq=A[ncol:],
+                               b_eq=b[ncol:], bounds=bounds, method="highs")
+    else:
+        res = optimize.linprog(cvec, A_eq=A, b_eq=b, bounds=bounds, method="highs")
     if res.status != 0:
         raise RuntimeError(res.message)
     x = res.x
-    y = res.eqlin.marginals
+    y = (np.concatenate([res.ineqlin.marginals, res.eqlin.marginals]) if capped
+         else res.eqlin.marginals)
     pi, u, v = [], [], []
     off = 0
     urow = 0

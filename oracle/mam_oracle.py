@@ -9,6 +9,7 @@ Everything is numpy float64, written step by step in the paper's order and
 notation (arXiv 2309.05315):
 
 * eq. (Delta), Remark 1 ......... ``project_simplex`` (sort-based, exact)
+* Delta_<=(tau) of the full unbalanced extension ... ``project_capped_simplex``
 * Prop. 2, eq. (pr)/(row_sol) ..... ``proj_balanced``
 * Section 5 ("Balanced and unbalanced settings") ... ``dist_balanced``
 * Section 4.3 "Storage complexity" (pruning), eq. (HugeLP) (cost) ... ``prepare``
@@ -72,6 +73,35 @@ def project_simplex(W, tau):
     lam_p = css[np.arange(Wp.shape[0]), K - 1] / K
     X[pos] = np.maximum(Wp - lam_p[:, None], 0.0)
     lam[pos] = lam_p
+    return X, lam
+
+
+# --------------------------------------------------------------------------
+# Projection onto Delta_<=(tau): the full unbalanced extension of the paper
+# (its section "Algorithm's Extension: the Full Unbalanced Setting").
+# --------------------------------------------------------------------------
+
+def project_capped_simplex(W, tau):
+    """Euclidean projection of each row of W onto Delta_<=(tau_i).
+
+    Delta_<=(tau) = {u >= 0 : sum(u) <= tau}.  The paper's two steps: clip,
+    w_check = max(w, 0); if sum(w_check) <= tau the clipped vector is the
+    projection, otherwise the projection is the one onto Delta_R(tau).  For
+    tau = 0 the set is {0}.
+
+    Returns (X, lam): lam[i] is 0 where the clipped vector is returned, the
+    simplex threshold of ``project_simplex`` otherwise.
+    """
+    W = np.atleast_2d(np.asarray(W, dtype=F64))
+    n, _ = W.shape
+    tau = np.broadcast_to(np.asarray(tau, dtype=F64), (n,))
+    X = np.maximum(W, 0.0)                     # first step: clip
+    lam = np.zeros(n)
+    over = X.sum(axis=1) > tau                 # second step where the mass exceeds tau
+    if np.any(over):
+        X_over, lam_over = project_simplex(W[over], tau[over])
+        X[over] = X_over
+        lam[over] = lam_over
     return X, lam
 
 
@@ -150,18 +180,24 @@ class Prepared:
         return len(self.q)
 
 
-def sq_euclid_cost(xi, zeta, alpha_m):
-    """c_{rs} = alpha_m ||xi_r - zeta_s||^2 (eq. HugeLP), shape (S, R)."""
+def sq_euclid_cost(xi, zeta, alpha_m, eta: float = 0.0):
+    """c_{rs} = alpha_m (||xi_r - zeta_s||^2 - eta), shape (S, R).
+
+    eta = 0 is eq. (HugeLP); eta > 0 is the shifted distance matrix of the
+    full unbalanced extension, alpha_m [d(xi_r, zeta_s) - eta].
+    """
     diff = zeta[:, None, :] - xi[None, :, :]
-    return alpha_m * np.einsum("srd,srd->sr", diff, diff)
+    return alpha_m * (np.einsum("srd,srd->sr", diff, diff) - eta)
 
 
-def prepare(problem, cost_dtype: str = "f64") -> Prepared:
+def prepare(problem, cost_dtype: str = "f64", eta: float = 0.0) -> Prepared:
     """Drop zero-weight columns (Section 4.3) and build the costs.
 
     The cost of measure m is alpha_m ||xi_r - zeta_s||^2 (eq. HugeLP), or
     alpha_m * C^(m) when the problem carries a general cost matrix C^(m)
     (the paper notes no assumption on the costs is needed, Section 2).
+    With eta > 0 (full unbalanced extension) the distance is shifted first:
+    alpha_m (||xi_r - zeta_s||^2 - eta), or alpha_m (C^(m) - eta).
     ``cost_dtype`` in {"f64", "f32", "bf16", "f16"} rounds the stored cost
     the way a reduced-precision store would (FP64 -> FP32 -> target).
     """
@@ -175,9 +211,9 @@ def prepare(problem, cost_dtype: str = "f64") -> Prepared:
         zs.append(np.asarray(problem.zeta[m], dtype=F64)[idx])
         S.append(len(idx))
         if problem.cost is not None:
-            cm = problem.alpha[m] * np.asarray(problem.cost[m], dtype=F64)[idx]
+            cm = problem.alpha[m] * (np.asarray(problem.cost[m], dtype=F64)[idx] - eta)
         else:
-            cm = sq_euclid_cost(xi, zs[-1], float(problem.alpha[m]))
+            cm = sq_euclid_cost(xi, zs[-1], float(problem.alpha[m]), eta)
         if cost_dtype == "f32":
             cm = cm.astype(np.float32).astype(F64)
         elif cost_dtype == "bf16":
@@ -244,7 +280,7 @@ def bundle_sequence(alpha, nb: int, seed: int, n_iters: int, start: int = 0):
 # Lagrangian lower bound of eq. (HugeLP) / (UWB).
 # --------------------------------------------------------------------------
 
-def lower_bound(prep: Prepared, v: Sequence[np.ndarray]) -> float:
+def lower_bound(prep: Prepared, v: Sequence[np.ndarray], capped: bool = False) -> float:
     """LB(v) = sum_m sum_s q_s min_r (c^(m)_{rs} - v^(m)_r).
 
     Relaxing the coupling rows sum_s pi^(m)_{rs} = p_r of eq. (HugeLP) with
@@ -253,10 +289,16 @@ def lower_bound(prep: Prepared, v: Sequence[np.ndarray]) -> float:
     column at the cheapest row.  For eq. (UWB) the same value is a lower
     bound whenever, in addition, sum_m S_m ||v^(m)||^2 <= gamma^2, because
     gamma dist_L(pi) >= <u, pi> for every u in L^perp with ||u|| <= gamma.
+    With capped columns (sum_r pi_{rs} <= q_s, the full unbalanced
+    extension) a column may also carry no mass, so its term is
+    q_s min(0, min_r (c_{rs} - v_r)).
     """
     tot = 0.0
     for m in range(prep.M):
-        tot += float(np.dot(prep.q[m], (prep.c[m] - v[m][None, :]).min(axis=1)))
+        col = (prep.c[m] - v[m][None, :]).min(axis=1)
+        if capped:
+            col = np.minimum(col, 0.0)
+        tot += float(np.dot(prep.q[m], col))
     return tot
 
 
@@ -267,17 +309,23 @@ def lower_bound(prep: Prepared, v: Sequence[np.ndarray]) -> float:
 class MamOracle:
     """Algorithm 1 (MAM), deterministic or randomized, balanced or not.
 
+    ``capped`` replaces the projection onto Delta_R(q_s) of Step 2 with the
+    one onto Delta_<=(q_s) (full unbalanced extension; its shifted cost is
+    built by ``prepare(..., eta=...)``).
+
     State: theta (list of (S_m, R) arrays) and the marginals p^(m) of the
     last update of each measure (Step 0 / Step 3).
     """
 
     def __init__(self, prep: Prepared, rho: float, gamma: float = math.inf,
-                 n_bundles: int = 1, seed: int = 0, theta0: str = "spread"):
+                 n_bundles: int = 1, seed: int = 0, theta0: str = "spread",
+                 capped: bool = False):
         if rho <= 0:
             raise ValueError("rho must be positive")
         self.prep = prep
         self.rho = float(rho)
         self.gamma = float(gamma)
+        self.capped = bool(capped)
         self.nb = max(1, int(n_bundles))
         self.seed = int(seed)
         self.B = bundles(prep.M, self.nb)
@@ -333,7 +381,10 @@ class MamOracle:
         for m in Mk:                                          # Step 2
             d = d_all[m]
             w = self.theta[m] + 2.0 * d[None, :] - prep.c[m] / rho
-            pihat, lam = project_simplex(w, prep.q[m])
+            if self.capped:
+                pihat, lam = project_capped_simplex(w, prep.q[m])
+            else:
+                pihat, lam = project_simplex(w, prep.q[m])
             self.theta[m] = pihat - d[None, :]
             self.lam[m] = lam
             self.w_hat_m[m] = float(np.sum(prep.c[m] * pihat))
@@ -358,7 +409,7 @@ class MamOracle:
         w_hat = float(self.w_hat_m.sum())
         dist_hat = dist_balanced(self.phat_m, prep.S)
         f_unbal = w_hat + (0.0 if math.isinf(self.gamma) else self.gamma * dist_hat)
-        lb = lower_bound(prep, [self.rho * d for d in d_all])
+        lb = lower_bound(prep, [self.rho * d for d in d_all], self.capped)
         return {"w_hat": w_hat, "dist_pihat": dist_hat, "f_unbal": f_unbal,
                 "lower_bound": lb}
 
