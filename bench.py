@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--rho", type=float, default=None,
                     help="rho of the time-to-gap measurement (default: the workload's)")
     ap.add_argument("--gap-ref-iters", type=int, default=50000)
+    ap.add_argument("--eta", type=float, default=None,
+                    help="capped columns (the full unbalanced extension: projection onto "
+                         "Delta_<=(q_s), cost alpha_m (d - eta)) with this eta")
     ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap measurement")
     ap.add_argument("--no-diff", action="store_true",
                     help="mixture workload: skip the forward+backward measurement")
@@ -178,7 +181,7 @@ class ClockSampler:
 
 
 def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
-                max_iters=50000, check_every=10, rho=None):
+                max_iters=50000, check_every=10, rho=None, ext=None):
     """Time to a 1e-4 objective gap.  The reference W* of each problem comes
     from a long run of its own: the largest dual lower bound seen (balanced)
     or the smallest F(pi-hat) seen (unbalanced).  Then, from theta^0, the
@@ -189,7 +192,7 @@ def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
     import math
     import torch
     from paper_2309_05315_gb300 import Mam
-    kw = dict(cost_dtype=cost_dtype, diag="last", rho=rho)
+    kw = dict(cost_dtype=cost_dtype, diag="last", rho=rho, **(ext or {}))
     make = (lambda: Mam(problems=probs, **kw)) if len(probs) > 1 else (lambda: Mam(probs[0], **kw))
     balanced = [math.isinf(getattr(p, "gamma", math.inf)) for p in probs]
     qa = []
@@ -283,6 +286,11 @@ def dist_env():
     return ws, rank, local
 
 
+def extension(args):
+    """Keyword arguments of the capped-column extension, or none."""
+    return {} if args.eta is None else {"capped": True, "eta": float(args.eta)}
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores (reference arm)."""
     ws, rank, _ = dist_env()
@@ -291,12 +299,14 @@ def run_reference(args):
     from oracle.mam_oracle import MamOracle, prepare
     probs, cost_dtype = workload(args.workload)
     prob = probs[0]
-    prep_full = prepare(prob)
+    ext = extension(args)
+    eta, capped = ext.get("eta", 0.0), ext.get("capped", False)
+    prep_full = prepare(prob, eta=eta)
     T = int(sum(prep_full.S))
     entries = T * prob.R
     # Each step is one oracle iteration over a bounded column sample of the
     # workload, sized so the whole run takes about two minutes.
-    orc_full = MamOracle(prep_full, prob.rho)
+    orc_full = MamOracle(prep_full, prob.rho, capped=capped)
     t0 = time.perf_counter()
     orc_full.step(diagnostics=False)
     per_entry = (time.perf_counter() - t0) / entries
@@ -312,7 +322,7 @@ def run_reference(args):
     sub.q = [mask / mask.sum() * prob.q[keep_m].sum()]
     sub.zeta = [sub.zeta[keep_m]]
     sub.alpha = np.array([1.0])
-    orc = MamOracle(prepare(sub), prob.rho)
+    orc = MamOracle(prepare(sub, eta=eta), prob.rho, capped=capped)
     for _ in range(args.warmup):
         orc.step(diagnostics=False)
     t0 = time.perf_counter()
@@ -323,6 +333,7 @@ def run_reference(args):
     value = args.steps * sample_entries / dt
     cfg = describe(args.workload, probs, "f64", T, entries)
     cfg["theta_dtype"] = "f64"
+    cfg.update(ext)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
@@ -337,10 +348,11 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline(prob, entries, seconds=12.0):
+def cpu_baseline(prob, entries, seconds=12.0, ext=None):
     from oracle.mam_oracle import MamOracle, prepare
-    prep = prepare(prob)
-    orc = MamOracle(prep, prob.rho)
+    ext = ext or {}
+    prep = prepare(prob, eta=ext.get("eta", 0.0))
+    orc = MamOracle(prep, prob.rho, capped=ext.get("capped", False))
     n = 0
     t0 = time.perf_counter()
     while True:
@@ -377,7 +389,8 @@ def main():
     # A dedicated (non-default) stream: the library orders its work on it and
     # the timing events below are recorded on the same stream.
     stream = torch.cuda.Stream()
-    kw = dict(cost_dtype=cost_dtype, diag="never", stream=stream)
+    ext = extension(args)
+    kw = dict(cost_dtype=cost_dtype, diag="never", stream=stream, **ext)
     gpu = Mam(problems=probs, **kw) if len(probs) > 1 else Mam(probs[0], **kw)
     if args.autotune:
         gpu.autotune(5)
@@ -431,6 +444,7 @@ def main():
     peak, peak_kind = peaks()
     achieved = alg_bytes / col_avg_s / 1e9
     cfg = describe(args.workload, probs, cost_dtype, gpu.T, gpu.T * gpu.R)
+    cfg.update(ext)
     cfg["l2"] = (f"inputs larger than L2: {alg_bytes / 1e6:.0f} MB of plan/cost traffic per "
                  "step, no flush")
     cfg["kernel_config"] = gpu.config()
@@ -457,8 +471,8 @@ def main():
     if not args.no_gap:
         line["time_to_gap"] = time_to_gap(probs, cost_dtype, rho=args.rho,
                                           ref_iters=args.gap_ref_iters,
-                                          max_iters=args.gap_ref_iters)
-    if args.workload == 4 and not args.no_diff:
+                                          max_iters=args.gap_ref_iters, ext=ext)
+    if args.workload == 4 and not args.no_diff and not ext:
         line["differentiation"] = forward_backward(probs[0])
 
     if not args.no_e2e:
@@ -466,8 +480,8 @@ def main():
         # the problem data), the same number of steps, barycenter (d2h).
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g2 = Mam(problems=probs, cost_dtype=cost_dtype, diag="never") if len(probs) > 1 \
-            else Mam(probs[0], cost_dtype=cost_dtype, diag="never")
+        g2 = Mam(problems=probs, cost_dtype=cost_dtype, diag="never", **ext) if len(probs) > 1 \
+            else Mam(probs[0], cost_dtype=cost_dtype, diag="never", **ext)
         g2.step(args.warmup + args.steps)
         pbar = g2.barycenter()
         dt = time.perf_counter() - t0
@@ -483,7 +497,7 @@ def main():
                                "mam_get_barycenter to host, wall clock"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(probs[0], probs[0].R * int(
-            sum(int((q > 0).sum()) for q in probs[0].q)))
+            sum(int((q > 0).sum()) for q in probs[0].q)), ext=ext)
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -95,7 +95,8 @@ typedef struct {
   double rho;           /* prox parameter of eq. (DR), > 0: the projected
                            vector is theta + 2 t d - c / rho (Alg. 1)        */
   double gamma;         /* unbalanced penalty >= 0; INFINITY = balanced.
-                           Balanced problems need equal total masses.        */
+                           Balanced problems need equal total masses unless
+                           capped is set.                                    */
   int32_t n_bundles;    /* 0 or 1: deterministic MAM (all measures each
                            iteration).  nb > 1: Remark 2, measures split into
                            nb contiguous bundles, bundle i drawn with
@@ -106,15 +107,32 @@ typedef struct {
   int32_t theta0_mode;  /* 0: theta^0_{rs} = q_s / R;  1: theta^0 = 0       */
   int32_t diag_mode;    /* mam_diag_mode                                     */
   void* stream;         /* cudaStream_t to order work on, or NULL            */
+  double eta;           /* capped only: mass penalty eta >= 0, finite; the
+                           cost becomes alpha_m (d - eta) (or alpha_m (C - eta)
+                           with a general cost).  Must be 0 when capped = 0. */
+  int32_t capped;       /* 0: Step 2 projects column s onto Delta_R(q_s), so
+                           every column carries its mass (Alg. 1).  1: the
+                           full unbalanced extension of the paper ("Algorithm's
+                           Extension: the Full Unbalanced Setting"): column s
+                           is projected onto Delta_<=(q_s) = {u >= 0 :
+                           sum u <= q_s} (clip at 0, then the simplex
+                           projection if the clipped mass exceeds q_s), so a
+                           column may carry less mass; masses may differ for
+                           any gamma.  All problems of a batch share it.
+                           Reverse mode needs capped = 0.                    */
 } mam_desc;
 
 /* Diagnostics of the most recent diagnostic iteration k (all FP64). */
 typedef struct {
-  double w_hat;        /* sum_m <c^(m), pi-hat^(m)>                         */
+  double w_hat;        /* sum_m <c^(m), pi-hat^(m)>.  Randomized index sets:
+                          each column contributes the value of its last
+                          diagnostic update (with MAM_DIAG_EVERY: its last
+                          update, stale columns included, as p^(m) are).   */
   double dist_pihat;   /* dist_L(pi-hat) = sqrt(sum_m ||p^ - p^^(m)||^2/S_m) */
   double lower_bound;  /* sum_m sum_s q_s min_r (c_rs - rho d^(m)_r): a valid
                           lower bound of eq. (HugeLP)/(UWB) (deterministic
-                          runs; randomized runs recompute it on demand)     */
+                          runs; randomized runs recompute it on demand).
+                          Capped columns take q_s min(0, min_r (...)).      */
   double f_unbal;      /* w_hat + gamma * dist_pihat (= w_hat if balanced) */
   double fp_resid;     /* ||theta^{k+1} - theta^k||_2 over updated columns  */
   double dp_norm;      /* ||p^{k+1} - p^k||_2                               */

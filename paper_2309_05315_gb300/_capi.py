@@ -31,7 +31,8 @@ class MamDesc(C.Structure):
                 ("rho", C.c_double), ("gamma", C.c_double),
                 ("n_bundles", C.c_int32), ("seed", C.c_uint64),
                 ("cost_dtype", C.c_int32), ("theta0_mode", C.c_int32),
-                ("diag_mode", C.c_int32), ("stream", C.c_void_p)]
+                ("diag_mode", C.c_int32), ("stream", C.c_void_p),
+                ("eta", C.c_double), ("capped", C.c_int32)]
 
 
 class MamObjective(C.Structure):

@@ -101,6 +101,11 @@ mam_status validate(const mam_desc* d, int idx) {
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "unknown diag_mode");
   if (d->n_bundles < 0 || d->n_bundles > d->M)
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "n_bundles must be in 0..M");
+  if (d->capped != 0 && d->capped != 1)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "capped must be 0 or 1");
+  if (!std::isfinite(d->eta) || d->eta < 0 || (!d->capped && d->eta != 0))
+    return fail(nullptr, MAM_ERR_INVALID_ARG,
+                p + "eta must be finite and >= 0, and 0 unless capped is set");
   long long tot = 0;
   for (int m = 0; m < d->M; ++m) {
     if (d->S[m] < 1)
@@ -133,10 +138,10 @@ mam_status validate(const mam_desc* d, int idx) {
       return fail(nullptr, MAM_ERR_INVALID_ARG,
                   p + "measure " + std::to_string(m) + " has no positive weight");
     if (m == 0) Q0 = Q;
-    if (std::isinf(d->gamma) && std::fabs(Q - Q0) > 1e-9 * Q0)
+    if (std::isinf(d->gamma) && !d->capped && std::fabs(Q - Q0) > 1e-9 * Q0)
       return fail(nullptr, MAM_ERR_INVALID_ARG,
                   p + "balanced problems (gamma = inf) need equal total masses; "
-                      "use a finite gamma for the unbalanced variant");
+                      "use a finite gamma or capped columns for the unbalanced variants");
     off += d->S[m];
   }
   return MAM_OK;
@@ -392,6 +397,8 @@ ColArgs col_args(const mam_problem* h) {
   a.ld = h->ld;
   a.stages = h->cfg.stages;
   a.bisect_depth = h->cfg.bisect_depth;
+  a.lam_floor = h->capped ? 0.f : -INFINITY;
+  a.lb_cap = h->capped ? 0.f : INFINITY;
   return a;
 }
 
@@ -473,7 +480,8 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
     // Lower bound of every measure for the v^k the column step just used
     // (the fused value covers only the drawn bundle).
     MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta32, h->t_used, h->meas_prob,
-                       h->rho_m, h->col_meas, h->T, h->R, h->ld, h->diag_lb,
+                       h->rho_m, h->col_meas, h->T, h->R, h->ld,
+                       h->capped ? 0.f : INFINITY, h->diag_lb,
                        h->stream),
              "lower-bound kernel");
   }
@@ -580,9 +588,10 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
     if (descs[i].R != descs[0].R || descs[i].dim != descs[0].dim ||
         descs[i].cost_dtype != descs[0].cost_dtype ||
         descs[i].diag_mode != descs[0].diag_mode ||
-        descs[i].theta0_mode != descs[0].theta0_mode)
+        descs[i].theta0_mode != descs[0].theta0_mode || descs[i].capped != descs[0].capped)
       return fail(nullptr, MAM_ERR_INVALID_ARG,
-                  "batched problems must share R, dim, cost_dtype, diag_mode and theta0_mode");
+                  "batched problems must share R, dim, cost_dtype, diag_mode, theta0_mode "
+                  "and capped");
   }
   if (n > 1)
     for (int i = 0; i < n; ++i)
@@ -602,6 +611,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   h->dim = d0.dim;
   h->ld = round_up(d0.R, 8);
   h->cost_dtype = d0.cost_dtype;
+  h->capped = d0.capped != 0;
   h->theta0_mode = d0.theta0_mode;
   h->diag_mode = d0.diag_mode;
   h->nb = (n == 1 && d0.n_bundles > 1) ? d0.n_bundles : 1;
@@ -626,7 +636,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   std::vector<double> q64;
   std::vector<float> q32;
   std::vector<int> col_meas;
-  std::vector<double> alpha_m;
+  std::vector<double> alpha_m, eta_m;
   long long uoff_global = 0;
   for (int i = 0; i < n; ++i) {
     const mam_desc& d = descs[i];
@@ -650,6 +660,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
       h->a.push_back(am);
       h->meas_prob_h.push_back(i);
       alpha_m.push_back(d.alpha[m]);
+      eta_m.push_back(d.eta);
       double Q = 0;
       for (int s = 0; s < d.S[m]; ++s) {
         const double v = d.q[uoff + s];
@@ -758,6 +769,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->irho_m, size_t(h->Mtot), "rho table");
   ALLOC(h->a_d, size_t(h->Mtot), "weights a");
   ALLOC(h->alpha_d, size_t(h->Mtot), "alpha");
+  ALLOC(h->eta_d, size_t(h->Mtot), "eta");
   ALLOC(h->S_d, size_t(h->Mtot), "sizes");
   ALLOC(h->Sd_d, size_t(h->Mtot), "sizes");
   ALLOC(h->invS_d, size_t(h->Mtot), "sizes");
@@ -786,6 +798,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   if ((s = upload(h, h->irho_m, irho_m.data(), irho_m.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->a_d, h->a.data(), h->a.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->alpha_d, alpha_m.data(), alpha_m.size())) != MAM_OK) return bail(s);
+  if ((s = upload(h, h->eta_d, eta_m.data(), eta_m.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->S_d, h->S.data(), h->S.size())) != MAM_OK) return bail(s);
   {
     std::vector<double> Sd(h->Mtot), iS(h->Mtot);
@@ -870,7 +883,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
         e = cudaMemcpy(zeta_d, zk.data(), sizeof(double) * zk.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { s = cuda_fail(h, e, "zeta upload"); break; }
         e = launch_build_cost(h->cost_dtype, h->cost, xi_d, zeta_d, nullptr,
-                              h->col_meas, h->alpha_d, c0, c1 - c0, h->R, h->ld,
+                              h->col_meas, h->alpha_d, h->eta_d, c0, c1 - c0, h->R, h->ld,
                               h->dim, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { s = cuda_fail(h, e, "cost kernel"); break; }
@@ -898,7 +911,8 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
           e = cudaMemcpy(gen_d, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice);
           if (e == cudaSuccess)
             e = launch_build_cost(h->cost_dtype, h->cost, xi_d, nullptr, gen_d, h->col_meas,
-                                  h->alpha_d, cb, ce - cb, h->R, h->ld, h->dim, h->stream);
+                                  h->alpha_d, h->eta_d, cb, ce - cb, h->R, h->ld, h->dim,
+                                  h->stream);
           if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
           if (e != cudaSuccess) s = cuda_fail(h, e, "cost kernel");
         }

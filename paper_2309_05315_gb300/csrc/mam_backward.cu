@@ -126,6 +126,9 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   if (!h) return fail(nullptr, MAM_ERR_INVALID_ARG, "null handle");
   if (h->failed) return MAM_ERR_STATE;
   if (h->P != 1) return fail(h, MAM_ERR_INVALID_ARG, "differentiation needs a single problem");
+  if (h->capped)
+    return fail(h, MAM_ERR_INVALID_ARG,
+                "differentiation needs columns that carry their mass (capped = 0)");
   if (std::isfinite(h->gamma[0]))
     return fail(h, MAM_ERR_INVALID_ARG, "differentiation needs the balanced problem (gamma = inf)");
   if (h->nb != 1)

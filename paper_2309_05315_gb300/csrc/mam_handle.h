@@ -30,6 +30,7 @@ struct mam_problem {
   long long T = 0;
   int cost_dtype = 0, theta0_mode = 0, diag_mode = 0;
   int nb = 1;
+  bool capped = false;  // columns projected onto Delta_<=(q_s) (full unbalanced extension)
   unsigned long long seed = 0;
   bool has_gen_cost = false;
 
@@ -76,6 +77,7 @@ struct mam_problem {
   float* irho_m = nullptr;
   double* a_d = nullptr;
   double* alpha_d = nullptr;
+  double* eta_d = nullptr;  // [Mtot] eta of the measure's problem (capped; else 0)
   int* S_d = nullptr;
   double* Sd_d = nullptr;
   double* invS_d = nullptr;

@@ -63,6 +63,10 @@ struct ColArgs {
   int ld;                    // padded column stride (multiple of 8)
   int stages;                // TMA pipeline depth
   int bisect_depth;          // bisection steps on a cold start
+  float lam_floor;           // lower clamp of the applied threshold: -inf, or 0
+                             // for capped columns (projection onto Delta_<=(q_s))
+  float lb_cap;              // upper clamp of a column's lower-bound term per unit
+                             // mass: +inf, or 0 for capped columns
 };
 
 // Arguments of the averaging kernel (Algorithm 1, Step 3 completion, Step 1
@@ -123,8 +127,8 @@ cudaError_t column_ring_occupancy(int nv, int cost_dtype, bool diag, int threads
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const double* zeta, const double* gen_cost,
                               const int* col_meas, const double* alpha,
-                              long long col0, long long ncols, int R, int ld,
-                              int dim, cudaStream_t st);
+                              const double* eta, long long col0, long long ncols,
+                              int R, int ld, int dim, cudaStream_t st);
 cudaError_t launch_init_theta(float* theta, float* lam, float* nact, const double* q,
                               long long T, int R, int ld, int mode,
                               cudaStream_t st);
@@ -141,7 +145,7 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
                       const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
-                      float* diag_lb, cudaStream_t st);
+                      float lb_cap, float* diag_lb, cudaStream_t st);
 
 // out[i] = in[i] * scale (fixed-point marginals to FP64).
 cudaError_t launch_fx_to_double(const long long* in, size_t n, double scale, double* out,

@@ -310,8 +310,12 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
         }
       }
 
-      // Commit: theta' = pihat - d, Step 3 row sums (+ diagnostics).
-      const f2_t lf2 = pk(lam_fin, lam_fin);
+      // Commit: theta' = pihat - d, Step 3 row sums (+ diagnostics).  With
+      // capped columns (Delta_<=(q_s)) the threshold applied is
+      // max(lambda, 0): a simplex threshold at or below 0 means the clipped
+      // column already carries at most q_s.  lam_floor is -inf otherwise.
+      const float lam_use = fmaxf(lam_fin, A.lam_floor);
+      const f2_t lf2 = pk(lam_use, lam_use);
       float wc = 0.f, res = 0.f;
       float4* gth = reinterpret_cast<float4*>(A.theta + size_t(col) * ld);
 #pragma unroll
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
         if (tid == 0) {
           A.diag_wc[col] = wc;
           A.diag_res[col] = res;
-          A.diag_lb[col] = tau * lbmin;
+          A.diag_lb[col] = tau * fminf(lbmin, A.lb_cap);
         }
         refill(j);  // the reduction's barrier ended every read of stage s
       }
@@ -607,8 +611,8 @@ template <typename CT>
 __global__ void build_cost_kernel(CT* cost, const double* xi,
                                   const double* zeta, const double* gen,
                                   const int* col_meas, const double* alpha,
-                                  long long col0, long long ncols, int R,
-                                  int ld, int dim) {
+                                  const double* eta, long long col0,
+                                  long long ncols, int R, int ld, int dim) {
   const long long n = ncols * ld;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -618,15 +622,16 @@ __global__ void build_cost_kernel(CT* cost, const double* xi,
     double c = INFINITY;  // padding rows: w = -inf, never active
     if (r < R) {
       const double al = alpha[col_meas[col]];
+      const double et = eta ? eta[col_meas[col]] : 0.0;
       if (gen) {
-        c = __dmul_rn(al, gen[jc * R + r]);
+        c = __dmul_rn(al, __dadd_rn(gen[jc * R + r], -et));
       } else {
         double acc = 0.0;
         for (int k = 0; k < dim; ++k) {
           const double df = __dadd_rn(zeta[jc * dim + k], -xi[size_t(r) * dim + k]);
           acc = __dadd_rn(acc, __dmul_rn(df, df));
         }
-        c = __dmul_rn(al, acc);
+        c = __dmul_rn(al, __dadd_rn(acc, -et));
       }
     }
     cost[size_t(col) * ld + r] = to_cost<CT>(__double2float_rn(c));
@@ -719,7 +724,7 @@ template <typename CT>
 __global__ void __launch_bounds__(256) lb_kernel(
     const CT* cost, const float* q, const float* delta32, const double* t_used,
     const int* meas_prob, const float* rho, const int* col_meas, long long T,
-    int R, int ld, float* diag_lb) {
+    int R, int ld, float lb_cap, float* diag_lb) {
   const int lane = threadIdx.x & 31;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -739,7 +744,7 @@ __global__ void __launch_bounds__(256) lb_kernel(
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if (lane == 0) diag_lb[col] = q[col] * mn;
+    if (lane == 0) diag_lb[col] = q[col] * fminf(mn, lb_cap);
   }
 }
 
@@ -856,8 +861,8 @@ cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st) {
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const double* zeta, const double* gen_cost,
                               const int* col_meas, const double* alpha,
-                              long long col0, long long ncols, int R, int ld,
-                              int dim, cudaStream_t st) {
+                              const double* eta, long long col0, long long ncols,
+                              int R, int ld, int dim, cudaStream_t st) {
   const long long n = ncols * ld;
   long long g = (n + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
@@ -865,18 +870,18 @@ cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
   switch (cost_dtype) {
     case 0:
       build_cost_kernel<float><<<int(g), 256, 0, st>>>(
-          static_cast<float*>(cost), xi, zeta, gen_cost, col_meas, alpha, col0,
-          ncols, R, ld, dim);
+          static_cast<float*>(cost), xi, zeta, gen_cost, col_meas, alpha, eta,
+          col0, ncols, R, ld, dim);
       break;
     case 1:
       build_cost_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(
           static_cast<__nv_bfloat16*>(cost), xi, zeta, gen_cost, col_meas,
-          alpha, col0, ncols, R, ld, dim);
+          alpha, eta, col0, ncols, R, ld, dim);
       break;
     case 2:
       build_cost_kernel<__half><<<int(g), 256, 0, st>>>(
-          static_cast<__half*>(cost), xi, zeta, gen_cost, col_meas, alpha, col0,
-          ncols, R, ld, dim);
+          static_cast<__half*>(cost), xi, zeta, gen_cost, col_meas, alpha, eta,
+          col0, ncols, R, ld, dim);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -922,19 +927,19 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
                       const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
-                      float* diag_lb, cudaStream_t st) {
+                      float lb_cap, float* diag_lb, cudaStream_t st) {
   long long g = (T * 32 + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
   if (g < 1) g = 1;
   switch (cost_dtype) {
     case 0:
-      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     case 1:
-      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     case 2:
-      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, diag_lb);
+      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     default:
       return cudaErrorInvalidValue;

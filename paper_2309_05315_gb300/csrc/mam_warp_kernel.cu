@@ -299,7 +299,9 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
         if (lane == 0 && j + K < ncol) issue(j + K, s);
       }
       int np = 0;
-      const float lam = warp_search<NV>(w, tau, lam_prev, A.bisect_depth, np);
+      const float lam_s = warp_search<NV>(w, tau, lam_prev, A.bisect_depth, np);
+      // capped columns apply max(lambda, 0) (lam_floor = 0; -inf otherwise)
+      const float lam = fmaxf(lam_s, A.lam_floor);
       my_passes += np;
 
       // Commit: theta' = pihat - d (streaming stores), Step 3 row sums.
@@ -353,12 +355,12 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
         if (lane == 0) {
           A.diag_wc[col] = wc;
           A.diag_res[col] = res;
-          A.diag_lb[col] = tau * lbmin;
+          A.diag_lb[col] = tau * fminf(lbmin, A.lb_cap);
         }
         __syncwarp();
         if (lane == 0 && j + K < ncol) issue(j + K, s);
       }
-      if (lane == 0) A.lam[col] = lam;
+      if (lane == 0) A.lam[col] = lam_s;
     }
     if (lane == 0 && my_passes) atomicAdd(A.passes, my_passes);
     if (failed && lane == 0) atomicCAS(A.err, 0, 1);

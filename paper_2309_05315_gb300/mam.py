@@ -26,7 +26,7 @@ class _DescKeep:
     """Owns the contiguous arrays a mam_desc points into."""
 
     def __init__(self, problem, cost_dtype, theta0_mode, diag_mode, n_bundles,
-                 seed, rho, gamma, stream):
+                 seed, rho, gamma, stream, capped=False, eta=0.0):
         M = len(problem.q)
         xi = np.ascontiguousarray(problem.xi, dtype=np.float64)
         if xi.ndim == 1:
@@ -64,17 +64,24 @@ class _DescKeep:
         d.theta0_mode = {"spread": 0, "zero": 1}[theta0_mode]
         d.diag_mode = _capi.DIAG_MODES[diag_mode]
         d.stream = stream
+        d.eta = float(eta)
+        d.capped = 1 if capped else 0
         self.desc = d
 
 
 class Mam:
-    """One MAM problem (or a batch) living on the GPU."""
+    """One MAM problem (or a batch) living on the GPU.
+
+    ``capped=True`` selects the full unbalanced extension: columns are
+    projected onto Delta_<=(q_s) and the cost becomes alpha_m (d - eta).
+    """
 
     def __init__(self, problem=None, *, problems: Optional[Sequence] = None,
                  cost_dtype: str = "f32", theta0: str = "spread",
                  diag: str = "last", n_bundles: Optional[int] = None,
                  seed: int = 0, rho: Optional[float] = None,
-                 gamma: Optional[float] = None, stream=None):
+                 gamma: Optional[float] = None, stream=None,
+                 capped: bool = False, eta: float = 0.0):
         L = _capi.lib()
         if (problem is None) == (problems is None):
             raise ValueError("give exactly one of problem / problems")
@@ -82,7 +89,8 @@ class Mam:
         st = None
         if stream is not None:
             st = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-        keeps = [_DescKeep(p, cost_dtype, theta0, diag, n_bundles, seed, rho, gamma, st)
+        keeps = [_DescKeep(p, cost_dtype, theta0, diag, n_bundles, seed, rho, gamma, st,
+                           capped, eta)
                  for p in probs]
         self._h = C.c_void_p()
         if problems is None:

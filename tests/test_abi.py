@@ -67,6 +67,11 @@ def make_desc(M=2, R=4, S=(3, 3), q=None, gamma=math.inf, rho=1.0, **kw):
     dict(cost_dtype=7),
     dict(theta0_mode=3),
     dict(n_bundles=5),
+    dict(capped=2),
+    dict(capped=1, eta=-1.0),
+    dict(capped=1, eta=float("nan")),
+    dict(capped=1, eta=float("inf")),
+    dict(eta=0.5),  # eta without capped columns
 ])
 def test_invalid_descriptor_fields(L, case):
     d, keep = make_desc()
@@ -89,6 +94,19 @@ def test_invalid_weights(L, q):
     h = C.c_void_p()
     assert L.mam_create(C.byref(d), C.byref(h)) == 1
     assert not h.value
+
+
+def test_capped_columns_allow_unequal_masses(L):
+    """Validation accepts unequal masses when the columns are capped (the
+    call then fails later, on the device allocation of a GPU-less host, or
+    succeeds on a GPU)."""
+    q = [0.5, 0.5, 0.0, 0.4, 0.7, 0.0]
+    d, keep = make_desc(q=q, capped=1, eta=0.25)
+    h = C.c_void_p()
+    st = L.mam_create(C.byref(d), C.byref(h))
+    assert st != 1, L.mam_last_error(None)
+    if h.value:
+        L.mam_destroy(h)
 
 
 def test_null_arguments(L):

@@ -167,6 +167,10 @@ def test_backward_rejections(Mam):
         with pytest.raises(MamError) as e:
             g.forward_record(5, 1)
         assert e.value.status == 1
+    with Mam(prob, diag="never", capped=True, eta=0.01) as g:
+        with pytest.raises(MamError) as e:
+            g.forward_record(5, 1)
+        assert e.value.status == 1
 
 
 def test_torch_autograd_function(Mam):

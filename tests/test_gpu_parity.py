@@ -43,15 +43,15 @@ def flat(th):
 
 def compare_trajectory(Mam, prob, iters, cost_dtype="f32", oracle_cost="f64",
                        n_bundles=1, seed=0, gamma=None, theta0="spread",
-                       config=None, tol=ITER_TOL):
+                       config=None, tol=ITER_TOL, capped=False, eta=0.0):
     g = math.inf if gamma is None else gamma
-    prep = prepare(prob, oracle_cost)
+    prep = prepare(prob, oracle_cost, eta=eta)
     orc = MamOracle(prep, prob.rho, gamma=g, n_bundles=n_bundles, seed=seed,
-                    theta0=theta0)
+                    theta0=theta0, capped=capped)
     Q, Qa = masses(prep)
     worst = 0.0
     with Mam(prob, cost_dtype=cost_dtype, diag="never", n_bundles=n_bundles,
-             seed=seed, gamma=g, theta0=theta0) as gpu:
+             seed=seed, gamma=g, theta0=theta0, capped=capped, eta=eta) as gpu:
         if config:
             gpu.set_config(**config)
         assert gpu.T == sum(int(s) for s in prep.S)
@@ -224,6 +224,51 @@ def test_diagnostics_match_oracle(Mam):
         assert abs(o[k] - ref[k]) <= 1e-4 * abs(ref[k]), k
     assert abs(o["dist_pihat"] - ref["dist_pihat"]) <= 1e-3 * ref["dist_pihat"]
     assert abs(o["t"] - ref["t"]) <= 1e-4
+
+
+@pytest.mark.parametrize("gamma, cfg", [
+    (math.inf, None),                                   # ring kernel (R = 36)
+    (math.inf, dict(kind=0, threads=32, vec=1, stages=1)),
+    (0.02, None),
+    (0.02, dict(kind=0, threads=64, vec=1, stages=2)),
+])
+def test_capped_columns(Mam, gamma, cfg):
+    """Full unbalanced extension: unequal masses, cost alpha_m (d - eta) with
+    eta between the grid's squared distances, projection onto
+    Delta_<=(q_s)."""
+    prob = tiny_problem(13, M=3, K=6, rho=8.0, masses=[0.6, 1.0, 1.4])
+    worst = compare_trajectory(Mam, prob, 40, gamma=gamma, capped=True, eta=0.05,
+                               config=cfg)
+    assert worst >= 0.0
+
+
+def test_capped_columns_mixture_cta_kernel(Mam):
+    """R = 1600 mixture in the default one-CTA-per-column shape, capped."""
+    from workloads import config4
+    compare_trajectory(Mam, config4(), 3, capped=True, eta=0.01)
+
+
+@pytest.mark.parametrize("n_bundles", [1, 3])
+def test_capped_diagnostics_match_oracle(Mam, n_bundles):
+    """W-hat and the lower bound with capped columns (each column's bound
+    term is q_s min(0, min_r (c - rho d))), fused (deterministic) or
+    recomputed by the lower-bound kernel (randomized index sets).  With
+    randomized index sets every iteration is diagnostic, so that each
+    column's W-hat term is the one of its last update, as in the oracle."""
+    prob = tiny_problem(17, M=3, K=6, rho=8.0, masses=[0.8, 1.0, 1.2])
+    eta = 0.05
+    prep = prepare(prob, eta=eta)
+    orc = MamOracle(prep, prob.rho, n_bundles=n_bundles, seed=5, capped=True)
+    orc.run(29)
+    ref = orc.step(diagnostics=True)
+    diag = "every" if n_bundles > 1 else "last"
+    with Mam(prob, diag=diag, n_bundles=n_bundles, seed=5, capped=True, eta=eta) as gpu:
+        gpu.step(30)
+        o = gpu.objective()
+    scale = sum(float(np.abs(c).max()) * float(q.sum()) for c, q in zip(prep.c, prep.q))
+    for k in ("w_hat", "lower_bound"):
+        assert abs(o[k] - ref[k]) <= 1e-4 * scale, (k, o[k], ref[k])
+    assert o["lower_bound"] <= o["w_hat"] + 1e-4 * scale
 
 
 def test_bitwise_determinism_and_resume(Mam):
