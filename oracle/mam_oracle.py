@@ -15,6 +15,8 @@ notation (arXiv 2309.05315):
 * Section 4.3 "Storage complexity" (pruning), eq. (HugeLP) (cost) ... ``prepare``
 * Algorithm 1 (MAM), Remark 2 (bundles) ... ``MamOracle.step``
 * eq. (DR) + Lagrangian duality of eq. (HugeLP) ... ``lower_bound``
+* Prop. 4 and Algorithm 2 (free-support update) ... ``support_from_plans``,
+  ``MamOracle.update_support``
 
 Storage convention: the paper's plan theta^(m) is R x S_m.  Here each
 measure's plan is a numpy array of shape (S_m, R): row s holds the paper's
@@ -418,6 +420,52 @@ class MamOracle:
         for _ in range(n_iters):
             out = self.step(diagnostics)
         return out
+
+    def next_pihat(self):
+        """The projected plans pi-hat the next step would compute (Step 1 and
+        the projection of Step 2, without the theta update)."""
+        prep, rho = self.prep, self.rho
+        p, _, t = self.average()
+        out = []
+        for m in range(prep.M):
+            d = t * (p - self.pm[m]) / prep.S[m]
+            w = self.theta[m] + 2.0 * d[None, :] - prep.c[m] / rho
+            proj = project_capped_simplex if self.capped else project_simplex
+            out.append(proj(w, prep.q[m])[0])
+        return out
+
+    def update_support(self, eta: float = 0.0):
+        """Algorithm 2, support step: xi from Prop. 4 with the plans pi-hat of
+        the next step, then the costs of the new support (eta as in
+        ``prepare``).  theta and the marginals are kept (warm start)."""
+        prep = self.prep
+        xi = support_from_plans(prep.xi, prep.zeta, prep.alpha, self.next_pihat())
+        for m in range(prep.M):
+            prep.c[m] = sq_euclid_cost(xi, prep.zeta[m], float(prep.alpha[m]), eta)
+        prep.xi = xi
+        return xi
+
+
+# --------------------------------------------------------------------------
+# Free support: Prop. 4 (support step of Algorithm 2).
+# --------------------------------------------------------------------------
+
+def support_from_plans(xi, zeta, alpha, plans):
+    """xi_r = sum_m alpha_m sum_s zeta^(m)_s pi_{rs} / sum_m alpha_m sum_s pi_{rs}
+    (Prop. 4), the minimiser over xi of
+    Psi(xi) = sum_m alpha_m sum_{r,s} ||xi_r - zeta_s||^2 pi_{rs} / 2.
+    Rows that carry no mass keep their point.  ``plans`` are (S_m, R) arrays
+    like the oracle's plans."""
+    xi = np.asarray(xi, dtype=F64)
+    num = np.zeros_like(xi)
+    den = np.zeros(xi.shape[0])
+    for m, pl in enumerate(plans):
+        num += alpha[m] * (pl.T @ np.asarray(zeta[m], dtype=F64))
+        den += alpha[m] * pl.sum(axis=0)
+    out = xi.copy()
+    nz = den > 0
+    out[nz] = num[nz] / den[nz][:, None]
+    return out
 
 
 # --------------------------------------------------------------------------
