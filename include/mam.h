@@ -215,6 +215,24 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every);
 mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
                         double* grad_zeta, double* grad_xi);
 
+/* Free-support step of Algorithm 2 (Prop. 4).  From the current state, the
+ * plans pi-hat that the next column step would compute (Step 1 and the
+ * projection of Step 2, Algorithm 1; theta is not changed) give the new
+ * support
+ *   xi_r = sum_m alpha_m sum_s zeta_s pi-hat_rs / sum_m alpha_m sum_s pi-hat_rs,
+ * the minimiser of sum_m alpha_m sum_{r,s} ||xi_r - zeta_s||^2 pi-hat_rs; rows
+ * that carry no mass keep their point.  The costs are then rebuilt for the
+ * new support (FP64, rounded to the storage type; with eta when capped) and
+ * theta, the marginals and the thresholds are kept as the warm start of the
+ * following iterations.  Algorithm 2 alternates mam_step (or mam_solve) with
+ * this call.  The costs follow the support, not mam_get_state/mam_set_state.
+ * xi_out: host [R][dim], may be NULL; receives the new support.  Needs a
+ * single problem, support points with the squared Euclidean cost (no general
+ * cost matrix) and the deterministic index set, else MAM_ERR_INVALID_ARG.
+ * The per-row sums are 64-bit fixed point (order-independent).  Synchronises
+ * the handle's stream. */
+mam_status mam_update_support(mam_problem* h, double* xi_out);
+
 /* Kernel configuration of the column step.
  * kind 0: one CTA per column.  threads (multiple of 32, up to 1024 for vec
  *   1, 768 for 2, 512 for 3..4, 192 for 5..6, 384 for 8) x vec float4

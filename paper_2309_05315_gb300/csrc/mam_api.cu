@@ -673,6 +673,8 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
         }
       }
       Qa += am * Q;
+      h->alpha_h.push_back(d.alpha[m]);
+      h->Q_h.push_back(Q);
       h->col_off.push_back(h->col_off.back() + Sp[m]);
       h->unpruned_off.push_back(h->unpruned_off.back() + d.S[m]);
       uoff += d.S[m];
@@ -1052,6 +1054,82 @@ mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol, double w
   }
   if (iters_done) *iters_done = done;
   if (gap_out) *gap_out = gap;
+  return MAM_OK;
+}
+
+mam_status mam_update_support(mam_problem* h, double* xi_out) {
+  MAM_CHECK_HANDLE(h);
+  if (h->P != 1) return fail(h, MAM_ERR_INVALID_ARG, "the support step needs a single problem");
+  if (h->nb > 1)
+    return fail(h, MAM_ERR_INVALID_ARG, "the support step needs the deterministic index set");
+  if (h->has_gen_cost || h->zeta_kept.size() != size_t(h->T) * h->dim)
+    return fail(h, MAM_ERR_INVALID_ARG,
+                "the support step needs support points and the squared Euclidean cost");
+  mam_status s = MAM_OK;
+  if (!h->sup_acc) {  // first use: the buffers are published together
+    double *xd = nullptr, *zd = nullptr;
+    unsigned long long* ac = nullptr;
+    if ((s = dalloc(h, &xd, size_t(h->R) * h->dim, "support")) != MAM_OK) return s;
+    if ((s = dalloc(h, &zd, h->zeta_kept.size(), "support points")) != MAM_OK) return s;
+    if ((s = dalloc(h, &ac, size_t(h->R) * (h->dim + 1), "support sums")) != MAM_OK) return s;
+    if ((s = upload(h, xd, h->xi_h.data(), h->xi_h.size())) != MAM_OK) return s;
+    if ((s = upload(h, zd, h->zeta_kept.data(), h->zeta_kept.size())) != MAM_OK) return s;
+    MAM_CUDA(cudaMemsetAsync(ac, 0, sizeof(unsigned long long) * size_t(h->R) * (h->dim + 1),
+                             h->stream),
+             "memset");
+    h->xi_dev = xd;
+    h->zeta_dev = zd;
+    h->sup_acc = ac;
+  }
+  // t of the next step, from the averaging kernel's block sums (eq.
+  // Unbalanced-prox).
+  double t = 1.0;
+  if (!std::isinf(h->gamma[0])) {
+    const int nblk = avg_blocks(h);
+    std::vector<double> blk(size_t(nblk) * 4);
+    MAM_CUDA(cudaMemcpyAsync(blk.data(), h->blk, sizeof(double) * blk.size(),
+                             cudaMemcpyDeviceToHost, h->stream),
+             "read");
+    MAM_TRY(sync(h));
+    double e = 0;
+    for (int b = 0; b < nblk; ++b) e += blk[size_t(b) * 4];
+    const double rD = h->rho[0] * std::sqrt(e);
+    t = rD <= h->gamma[0] ? 1.0 : h->gamma[0] / rD;
+  }
+  // Fixed-point scale: every per-row sum stays below 2^61 in magnitude.
+  double zmax = 1.0, mass = 0.0;
+  for (double v : h->zeta_kept) zmax = std::max(zmax, std::fabs(v));
+  for (int m = 0; m < h->Mtot; ++m) mass += h->alpha_h[m] * h->Q_h[m];
+  if (!(mass > 0)) return fail(h, MAM_ERR_INVALID_ARG, "the support step needs sum alpha_m Q_m > 0");
+  SupportArgs a{};
+  a.theta = h->theta;
+  a.cost = h->cost;
+  a.q = h->q;
+  a.lam = h->lam;
+  a.col_meas = h->col_meas;
+  a.delta32 = h->delta32;
+  a.inv_rho = h->irho_m;
+  a.alpha = h->alpha_d;
+  a.zeta = h->zeta_dev;
+  a.acc = h->sup_acc;
+  a.fx = std::ldexp(1.0, int(std::floor(std::log2(std::ldexp(1.0, 61) / (1.01 * zmax * mass)))));
+  a.t = float(t);
+  a.lam_floor = h->capped ? 0.f : -INFINITY;
+  a.T = h->T;
+  a.R = h->R;
+  a.ld = h->ld;
+  a.dim = h->dim;
+  MAM_CUDA(launch_support_step(h->cost_dtype, a, h->xi_dev, h->stream), "support step");
+  // The costs of the new support (FP64, rounded to the storage type).
+  MAM_CUDA(launch_build_cost(h->cost_dtype, h->cost, h->xi_dev, h->zeta_dev, nullptr,
+                             h->col_meas, h->alpha_d, h->eta_d, 0, h->T, h->R, h->ld, h->dim,
+                             h->stream),
+           "cost kernel");
+  MAM_CUDA(cudaMemcpyAsync(h->xi_h.data(), h->xi_dev, sizeof(double) * h->xi_h.size(),
+                           cudaMemcpyDeviceToHost, h->stream),
+           "read");
+  MAM_TRY(sync(h));
+  if (xi_out) std::memcpy(xi_out, h->xi_h.data(), sizeof(double) * h->xi_h.size());
   return MAM_OK;
 }
 

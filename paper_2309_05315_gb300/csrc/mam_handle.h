@@ -78,6 +78,11 @@ struct mam_problem {
   double* a_d = nullptr;
   double* alpha_d = nullptr;
   double* eta_d = nullptr;  // [Mtot] eta of the measure's problem (capped; else 0)
+  // free-support step (allocated on first use)
+  double* xi_dev = nullptr;               // [R][dim]
+  double* zeta_dev = nullptr;             // [T][dim]
+  unsigned long long* sup_acc = nullptr;  // [R][dim + 1]
+  std::vector<double> alpha_h, Q_h;       // [Mtot] alpha_m and kept mass Q_m
   int* S_d = nullptr;
   double* Sd_d = nullptr;
   double* invS_d = nullptr;

@@ -158,6 +158,14 @@ class Mam:
         self._check(_capi.lib().mam_get_barycenter(self._h, out.ctypes.data, 0))
         return out if self.batched else out[0]
 
+    def update_support(self) -> np.ndarray:
+        """Free-support step (Algorithm 2, Prop. 4): moves the support to the
+        weighted means of the next step's plans, rebuilds the costs and
+        returns the new support [R, dim]."""
+        out = np.empty((self.R, self.dim), dtype=np.float64)
+        self._check(_capi.lib().mam_update_support(self._h, out.ctypes.data))
+        return out
+
     def barycenter_into(self, tensor):
         """Copy p into a CUDA float64 tensor of n_problems*R elements."""
         assert tensor.is_cuda and tensor.dtype.is_floating_point and tensor.element_size() == 8

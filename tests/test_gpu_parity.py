@@ -271,6 +271,72 @@ def test_capped_diagnostics_match_oracle(Mam, n_bundles):
     assert o["lower_bound"] <= o["w_hat"] + 1e-4 * scale
 
 
+def support_error(orc, eta, xi_gpu):
+    """Oracle support step; returns the mass-weighted mean distance between
+    the two new supports (rows weighted by sum_m alpha_m sum_s pi-hat_rs: a
+    row whose only mass is an entry at the threshold may differ between FP32
+    and FP64, and carries no weight)."""
+    plans = orc.next_pihat()
+    den = sum(orc.prep.alpha[m] * plans[m].sum(axis=0) for m in range(orc.prep.M))
+    xi_o = orc.update_support(eta)
+    dist = np.linalg.norm(xi_gpu - xi_o, axis=1)
+    return float(np.dot(den, dist) / den.sum())
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(gamma=0.02), dict(capped=True, eta=0.05)])
+def test_support_step_matches_oracle(Mam, kw):
+    """Algorithm 2: three rounds of 20 MAM iterations and a support step
+    (Prop. 4), then 10 more iterations on the rebuilt costs."""
+    gamma = kw.get("gamma", math.inf)
+    capped, eta = kw.get("capped", False), kw.get("eta", 0.0)
+    unequal = None if (math.isinf(gamma) and not capped) else [0.7, 1.0, 1.3]
+    prob = tiny_problem(31, M=3, K=6, rho=8.0, masses=unequal)
+    prep = prepare(prob, eta=eta)
+    orc = MamOracle(prep, prob.rho, gamma=gamma, capped=capped)
+    Q, _ = masses(prep)
+    with Mam(prob, diag="never", gamma=gamma, capped=capped, eta=eta) as gpu:
+        for _ in range(3):
+            orc.run(20)
+            gpu.step(20)
+            xi_g = gpu.update_support()
+            assert support_error(orc, eta, xi_g) <= 1e-5
+        orc.run(10)
+        gpu.step(10)
+        e_th = np.abs(gpu.theta().astype(np.float64).ravel() - flat(orc.theta)).sum() / Q
+        assert e_th <= 1e-4, e_th
+
+
+def test_support_step_mixture_full_size(Mam):
+    """R = 1600 mixture: 5 iterations, then the support step."""
+    from workloads import config4
+    prob = config4()
+    orc = MamOracle(prepare(prob), prob.rho)
+    with Mam(prob, diag="never") as gpu:
+        orc.run(5)
+        gpu.step(5)
+        xi_g = gpu.update_support()
+    assert support_error(orc, 0.0, xi_g) <= 1e-5
+
+
+def test_support_step_rejections(Mam):
+    from paper_2309_05315_gb300 import MamError
+    prob = tiny_problem(33, M=3, K=4, rho=8.0)
+    with Mam(prob, diag="never", n_bundles=3) as g:
+        with pytest.raises(MamError) as e:
+            g.update_support()
+        assert e.value.status == 1
+    gen = copy.deepcopy(prob)
+    gen.cost = [np.ones((len(q), prob.R)) for q in prob.q]
+    with Mam(gen, diag="never") as g:
+        with pytest.raises(MamError) as e:
+            g.update_support()
+        assert e.value.status == 1
+    with Mam(problems=[prob, prob], diag="never") as g:
+        with pytest.raises(MamError) as e:
+            g.update_support()
+        assert e.value.status == 1
+
+
 def test_bitwise_determinism_and_resume(Mam):
     prob = config1()
     with Mam(prob, diag="never") as a, Mam(prob, diag="never") as b:
