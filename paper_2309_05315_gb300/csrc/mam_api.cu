@@ -7,6 +7,7 @@
 // graph), diagnostics, checkpoints and kernel configuration.
 #include "mam.h"
 #include "mam_internal.h"
+#include "mam_support.h"
 #include "mam_handle.h"
 
 #include <algorithm>

@@ -14,7 +14,7 @@
 // the order of the adds).  A second kernel forms the ratios.  This is a
 // rare operation, kept apart from the per-iteration kernels.
 #include "mam_device.cuh"
-#include "mam_internal.h"
+#include "mam_support.h"
 
 #include <type_traits>
 
