@@ -297,6 +297,15 @@ mam_status mam_column_update_noalloc(float* theta, const float* cost, const floa
 /* Last error message of h, or the thread-local one when h is NULL. */
 const char* mam_last_error(const mam_problem* h);
 
+/* Self-test of failure detection: one warp waits, through the bounded
+ * mbarrier wait the column kernels use, on a phase that expects two
+ * arrivals and receives none.  The wait gives up after limit_us
+ * microseconds (1..2000000) and the call returns MAM_ERR_TIMEOUT, the status
+ * a real run reports when a device wait runs out; the CUDA context stays
+ * usable.  MAM_ERR_STATE if the wait did not run out, MAM_ERR_CUDA on a
+ * launch error.  Uses the current device and synchronises it. */
+mam_status mam_selftest_wait_timeout(int32_t limit_us);
+
 /* Free everything the handle owns; NULL is allowed. */
 void mam_destroy(mam_problem* h);
 
