@@ -92,7 +92,8 @@ typedef struct {
   const double* cost;   /* host [sum S][R] general cost C (row s of measure m
                            = column s of C^(m)), or NULL for squared
                            Euclidean.  Scaled by alpha_m either way.         */
-  double rho;           /* prox parameter of eq. (DR), > 0: the projected
+  double rho;           /* prox parameter of eq. (DR), in [1e-30, 1e30] (the
+                           kernels use rho and 1/rho in FP32): the projected
                            vector is theta + 2 t d - c / rho (Alg. 1)        */
   double gamma;         /* unbalanced penalty >= 0; INFINITY = balanced.
                            Balanced problems need equal total masses unless

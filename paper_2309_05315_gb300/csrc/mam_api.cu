@@ -92,6 +92,9 @@ mam_status validate(const mam_desc* d, int idx) {
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "zeta is required without a cost matrix");
   if (!(d->rho > 0) || !std::isfinite(d->rho))
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "rho must be finite and > 0");
+  // the kernels use rho and 1/rho in FP32
+  if (d->rho < 1e-30 || d->rho > 1e30)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "rho must lie in [1e-30, 1e30]");
   if (std::isnan(d->gamma) || d->gamma < 0)
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "gamma must be >= 0 (or INFINITY)");
   if (d->cost_dtype < 0 || d->cost_dtype > 2)

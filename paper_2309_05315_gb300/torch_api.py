@@ -71,16 +71,19 @@ def unrolled_barycenter(q, zeta, xi, S, alpha, rho=100.0, K=200, ckpt_every=20,
 
 
 def solve(q, zeta, xi, S, alpha, rho=100.0, gamma=math.inf, max_iters=20000, gap_tol=1e-4,
-          check_every=10, cost_dtype="f32", n_bundles=1, seed=0):
+          check_every=10, cost_dtype="f32", n_bundles=1, seed=0, capped=False, eta=0.0):
     """MAM to a relative gap of gap_tol (mam_solve) on torch's current CUDA
     stream; returns (p, info).  p is a float64 tensor [R] on the device of q
     (copied device to device from the library), info has the iterations run,
-    the last gap and the diagnostics of mam_objective."""
+    the last gap and the diagnostics of mam_objective.  ``capped``/``eta``
+    select the full unbalanced extension (columns projected onto
+    Delta_<=(q_s), cost alpha_m (d - eta))."""
     prob = _problem(q, zeta, xi, S, alpha, rho)
     prob.gamma = float(gamma)
     prob.n_bundles = int(n_bundles)
     stream = torch.cuda.current_stream(q.device if q.is_cuda else None)
-    with Mam(prob, cost_dtype=cost_dtype, diag="never", seed=seed, stream=stream) as g:
+    with Mam(prob, cost_dtype=cost_dtype, diag="never", seed=seed, stream=stream,
+             capped=capped, eta=eta) as g:
         iters, gap = g.solve(int(max_iters), float(gap_tol), 0.0, int(check_every))
         info = dict(g.objective(), iterations=iters, gap=gap)
         dev = q.device if q.is_cuda else torch.device("cuda")

@@ -63,6 +63,8 @@ def make_desc(M=2, R=4, S=(3, 3), q=None, gamma=math.inf, rho=1.0, **kw):
     dict(dim=4),
     dict(rho=0.0),
     dict(rho=-1.0),
+    dict(rho=1e-35),
+    dict(rho=1e35),
     dict(gamma=-0.5),
     dict(cost_dtype=7),
     dict(theta0_mode=3),
