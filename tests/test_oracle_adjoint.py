@@ -11,7 +11,7 @@ import copy
 import numpy as np
 import pytest
 
-from oracle.mam_oracle import unrolled_loss, unrolled_loss_and_grad
+from oracle.mam_oracle import MamOracle, prepare, unrolled_loss, unrolled_loss_and_grad
 from workloads import tiny_problem
 
 
@@ -74,3 +74,33 @@ def test_zero_iterations_gradient_is_closed_form():
         expect = np.where(prob.q[m] > 0, a[m] * g.sum() / prob.R, 0.0)
         np.testing.assert_allclose(gq[m], expect, rtol=1e-12)
     assert np.all(gxi == 0)
+
+
+@pytest.mark.parametrize("which", ["q", "zeta", "xi"])
+def test_dot_product_with_a_random_cotangent(which):
+    """<J v, w> = <v, J^T w> for a random cotangent w of p^K (not only the
+    loss residual) and a random direction v.  With target = p^K - w / 2 at
+    the base point, the gradient of ||p^K - target||^2 is J^T w, and central
+    differences of the same loss give <J v, w>."""
+    prob = tiny_problem(50, M=3, K=3, rho=4.0, density=0.8)
+    K = 10
+    rng = np.random.default_rng(7)
+    orc = MamOracle(prepare(prob, "f64"), prob.rho)
+    orc.run(K)
+    pK = orc.barycenter()
+    w = rng.normal(size=prob.R)
+    target = pK - 0.5 * w
+    _, gq, gz, gxi = unrolled_loss_and_grad(prob, K, prob.rho, target)
+    if which == "q":
+        v = [np.where(q > 0, rng.normal(size=q.shape) * q, 0.0) for q in prob.q]
+        adj = sum(float(np.dot(gq[m], v[m])) for m in range(prob.M))
+    elif which == "zeta":
+        v = [rng.normal(size=z.shape) for z in prob.zeta]
+        adj = sum(float(np.sum(gz[m] * v[m])) for m in range(prob.M))
+    else:
+        v = rng.normal(size=prob.xi.shape)
+        adj = float(np.sum(gxi * v))
+    h = 1e-6
+    tangent = (unrolled_loss(perturbed(prob, which, v, h), K, prob.rho, target)
+               - unrolled_loss(perturbed(prob, which, v, -h), K, prob.rho, target)) / (2 * h)
+    assert abs(tangent - adj) <= 1e-6 * max(abs(adj), 1e-6), (tangent, adj)
