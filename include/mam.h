@@ -234,6 +234,17 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
  * the handle's stream. */
 mam_status mam_update_support(mam_problem* h, double* xi_out);
 
+/* Algorithm 2 (free-support barycenter): `outer` rounds of
+ *   (a) Algorithm 1 on the current support: inner_iters iterations
+ *       (gap_tol = 0), or mam_solve to gap_tol with at most inner_iters
+ *       iterations and a check every check_every (gap_tol > 0);
+ *   (b) mam_update_support (Prop. 4).
+ * theta is kept across rounds.  xi_out (host [R][dim], may be NULL) receives
+ * the last support; iters_done (may be NULL) the iterations run.  Same
+ * requirements and errors as mam_update_support and mam_solve. */
+mam_status mam_free_support(mam_problem* h, int32_t outer, int32_t inner_iters, double gap_tol,
+                            int32_t check_every, double* xi_out, int32_t* iters_done);
+
 /* Kernel configuration of the column step.
  * kind 0: one CTA per column.  threads (multiple of 32, up to 1024 for vec
  *   1, 768 for 2, 512 for 3..4, 192 for 5..6, 384 for 8) x vec float4

@@ -468,6 +468,20 @@ def support_from_plans(xi, zeta, alpha, plans):
     return out
 
 
+def free_support(problem, outer: int, inner: int, eta: float = 0.0,
+                 gamma: float = math.inf, capped: bool = False):
+    """Algorithm 2: ``outer`` rounds of (``inner`` iterations of Algorithm 1
+    on the current support, then the support step of Prop. 4).  theta is
+    kept across rounds.  Returns the oracle (its prep holds the last
+    support and costs)."""
+    prep = prepare(problem, eta=eta)
+    orc = MamOracle(prep, problem.rho, gamma=gamma, capped=capped)
+    for _ in range(outer):
+        orc.run(inner)
+        orc.update_support(eta)
+    return orc
+
+
 # --------------------------------------------------------------------------
 # Reverse mode through K unrolled iterations (balanced, deterministic).
 # --------------------------------------------------------------------------

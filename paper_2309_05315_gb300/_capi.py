@@ -75,6 +75,8 @@ _SIGS = {
     "mam_objective_all": (C.c_int, [C.c_void_p, C.POINTER(MamObjective)]),
     "mam_get_barycenter": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "mam_update_support": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mam_free_support": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                   C.c_void_p, C.c_void_p]),
     "mam_selftest_wait_timeout": (C.c_int, [C.c_int32]),
     "mam_get_theta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mam_get_marginals": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),

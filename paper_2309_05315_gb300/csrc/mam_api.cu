@@ -1137,6 +1137,29 @@ mam_status mam_update_support(mam_problem* h, double* xi_out) {
   return MAM_OK;
 }
 
+mam_status mam_free_support(mam_problem* h, int32_t outer, int32_t inner_iters, double gap_tol,
+                            int32_t check_every, double* xi_out, int32_t* iters_done) {
+  MAM_CHECK_HANDLE(h);
+  if (outer < 0 || inner_iters < 0 || check_every < 1 || !(gap_tol >= 0))
+    return fail(h, MAM_ERR_INVALID_ARG, "bad free-support arguments");
+  int total = 0;
+  for (int k = 0; k < outer; ++k) {
+    // Algorithm 2: the fixed-support problem on the current support ...
+    int done = 0;
+    if (gap_tol > 0) {
+      MAM_TRY(mam_solve(h, inner_iters, gap_tol, 0.0, check_every, &done, nullptr));
+    } else {
+      MAM_TRY(mam_step(h, inner_iters));
+      done = inner_iters;
+    }
+    total += done;
+    // ... then the support step of Prop. 4 (costs rebuilt, theta kept).
+    MAM_TRY(mam_update_support(h, xi_out));
+  }
+  if (iters_done) *iters_done = total;
+  return MAM_OK;
+}
+
 mam_status mam_get_barycenter(mam_problem* h, double* p_out, int32_t device_ptr) {
   MAM_CHECK_HANDLE(h);
   if (!p_out) return fail(h, MAM_ERR_INVALID_ARG, "p_out is NULL");

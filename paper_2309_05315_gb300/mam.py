@@ -166,6 +166,18 @@ class Mam:
         self._check(_capi.lib().mam_update_support(self._h, out.ctypes.data))
         return out
 
+    def free_support(self, outer: int, inner_iters: int, gap_tol: float = 0.0,
+                     check_every: int = 10):
+        """Algorithm 2: ``outer`` rounds of Algorithm 1 (``inner_iters``
+        iterations, or to ``gap_tol``) followed by the support step.
+        Returns (support [R, dim], iterations run)."""
+        out = np.empty((self.R, self.dim), dtype=np.float64)
+        it = C.c_int32()
+        self._check(_capi.lib().mam_free_support(self._h, int(outer), int(inner_iters),
+                                                 float(gap_tol), int(check_every),
+                                                 out.ctypes.data, C.byref(it)))
+        return out, it.value
+
     def barycenter_into(self, tensor):
         """Copy p into a CUDA float64 tensor of n_problems*R elements."""
         assert tensor.is_cuda and tensor.dtype.is_floating_point and tensor.element_size() == 8

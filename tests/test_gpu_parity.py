@@ -318,6 +318,29 @@ def test_support_step_mixture_full_size(Mam):
     assert support_error(orc, 0.0, xi_g) <= 1e-5
 
 
+def test_free_support_rounds_match_oracle(Mam):
+    """Algorithm 2 through mam_free_support: 3 rounds of 30 iterations and a
+    support step, against the oracle's driver; then the barycenter."""
+    from oracle.mam_oracle import free_support
+    prob = tiny_problem(35, M=3, K=6, rho=8.0)
+    orc = MamOracle(prepare(prob), prob.rho)
+    for _ in range(3):  # the oracle's rounds, keeping the last round's row masses
+        orc.run(30)
+        plans = orc.next_pihat()
+        weight = sum(orc.prep.alpha[m] * plans[m].sum(axis=0) for m in range(orc.prep.M))
+        orc.update_support()
+    ref = free_support(prob, outer=3, inner=30)   # the oracle's own driver agrees
+    np.testing.assert_array_equal(ref.prep.xi, orc.prep.xi)
+    with Mam(prob, diag="never") as gpu:
+        xi_g, iters = gpu.free_support(3, 30)
+        p_g = gpu.barycenter()
+    assert iters == 90
+    d = np.linalg.norm(xi_g - orc.prep.xi, axis=1)
+    assert float(np.dot(weight, d) / weight.sum()) <= 1e-5
+    Qa = sum(orc.prep.a[m] * float(orc.prep.q[m].sum()) for m in range(orc.prep.M))
+    assert np.abs(p_g - orc.barycenter()).sum() / Qa <= 1e-4
+
+
 def test_support_step_rejections(Mam):
     from paper_2309_05315_gb300 import MamError
     prob = tiny_problem(33, M=3, K=4, rho=8.0)

@@ -16,7 +16,7 @@ import pytest
 from scipy import optimize
 
 from oracle.lp import solve_barycenter_lp
-from oracle.mam_oracle import MamOracle, prepare, support_from_plans
+from oracle.mam_oracle import MamOracle, free_support, prepare, support_from_plans
 from workloads import tiny_problem
 
 
@@ -116,3 +116,15 @@ def test_support_step_from_converged_mam_plans():
     assert opt_new <= plan_cost(prep_new, plans) * (1 + 1e-9)
     # the oracle's costs now belong to the new support
     np.testing.assert_allclose(orc.prep.c[0], prep_new.c[0], rtol=1e-12, atol=1e-15)
+
+
+def test_free_support_rounds_lower_the_lp_optimum():
+    """Algorithm 2 with MAM run close to convergence in every round: the
+    barycenter LP optimum at the final support is below the one at the
+    initial grid (each round is a block coordinate step)."""
+    prob = tiny_problem(27, M=3, K=3, rho=5.0)
+    opt0 = solve_barycenter_lp(prepare(prob))["opt"]
+    orc = free_support(prob, outer=3, inner=4000)
+    opt3 = solve_barycenter_lp(prepare(with_support(prob, orc.prep.xi)))["opt"]
+    assert opt3 <= opt0 * (1 + 1e-9)
+    assert opt3 < opt0 * 0.999  # the grid was not already optimal
