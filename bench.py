@@ -211,7 +211,7 @@ def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
     def gaps(objs):
         out = []
         for i, o in enumerate(objs):
-            gp = abs(o["f_unbal"] - wstar[i]) / abs(wstar[i])
+            gp = abs(o["f_unbal"] - wstar[i]) / max(abs(wstar[i]), 1e-300)
             if balanced[i]:
                 gp = max(gp, o["dist_pihat"] / qa[i])
             out.append(gp)
