@@ -1116,7 +1116,10 @@ mam_status mam_update_support(mam_problem* h, double* xi_out) {
   a.alpha = h->alpha_d;
   a.zeta = h->zeta_dev;
   a.acc = h->sup_acc;
-  a.fx = std::ldexp(1.0, int(std::floor(std::log2(std::ldexp(1.0, 61) / (1.01 * zmax * mass)))));
+  {
+    const double ex = std::floor(std::log2(std::ldexp(1.0, 61) / (1.01 * zmax * mass)));
+    a.fx = std::ldexp(1.0, int(std::max(-960.0, std::min(960.0, ex))));  // finite scale
+  }
   a.t = float(t);
   a.lam_floor = h->capped ? 0.f : -INFINITY;
   a.T = h->T;
