@@ -1159,6 +1159,8 @@ mam_status mam_free_support(mam_problem* h, int32_t outer, int32_t inner_iters, 
     // ... then the support step of Prop. 4 (costs rebuilt, theta kept).
     MAM_TRY(mam_update_support(h, xi_out));
   }
+  if (outer == 0 && xi_out && h->xi_h.size() == size_t(h->R) * h->dim)
+    std::memcpy(xi_out, h->xi_h.data(), sizeof(double) * h->xi_h.size());  // unchanged support
   if (iters_done) *iters_done = total;
   return MAM_OK;
 }
