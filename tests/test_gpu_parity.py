@@ -332,6 +332,9 @@ def test_free_support_rounds_match_oracle(Mam):
     ref = free_support(prob, outer=3, inner=30)   # the oracle's own driver agrees
     np.testing.assert_array_equal(ref.prep.xi, orc.prep.xi)
     with Mam(prob, diag="never") as gpu:
+        xi0, it0 = gpu.free_support(0, 30)   # no round: the support as given
+        np.testing.assert_array_equal(xi0, prob.xi)
+        assert it0 == 0
         xi_g, iters = gpu.free_support(3, 30)
         p_g = gpu.barycenter()
     assert iters == 90
