@@ -25,10 +25,10 @@ contiguous, as in the CUDA library.
 
 Parity pins (see tests/test_oracle_*.py): every function here is checked
 against brute force, closed forms, least squares, the HiGHS LP optimum, the
-exact DR fixed point built from LP duals, finite differences and invariants.
-Nothing here is "parity unpinned" except the unbalanced objective value,
-which the paper never prints (its iterates are pinned through Prop. 1 and the
-prox identity of eq. Unbalanced-prox).
+exact DR fixed point built from LP duals, finite differences, invariants,
+hand-derived IEEE 754 rounding results (``round_to_bf16``/``round_to_f16``),
+a hand-worked dist_L example, and the minimum of eq. (UWB) from a general
+constrained solver (the unbalanced objective F).
 """
 from __future__ import annotations
 
