@@ -308,6 +308,22 @@ def lower_bound(prep: Prepared, v: Sequence[np.ndarray], capped: bool = False) -
 # Algorithm 1.
 # --------------------------------------------------------------------------
 
+def column_step(theta_m, d, c_m, q_m, rho, capped=False):
+    """Step 2 of Algorithm 1 for the plan of one measure.
+
+    w = theta + 2 d - c / rho column by column, pi-hat = the projection of
+    each column onto Delta_R(q_s) (onto Delta_<=(q_s) when ``capped``), and
+    theta' = pi-hat - d.  Returns (theta', thresholds, <c, pi-hat>, row sums
+    of pi-hat).
+    """
+    w = theta_m + 2.0 * d[None, :] - c_m / rho
+    if capped:
+        pihat, lam = project_capped_simplex(w, q_m)
+    else:
+        pihat, lam = project_simplex(w, q_m)
+    return pihat - d[None, :], lam, float(np.sum(c_m * pihat)), pihat.sum(axis=0)
+
+
 class MamOracle:
     """Algorithm 1 (MAM), deterministic or randomized, balanced or not.
 
@@ -381,16 +397,9 @@ class MamOracle:
         Mk = self.index_set()
         d_all = [t * (p - self.pm[m]) / S[m] for m in range(prep.M)]
         for m in Mk:                                          # Step 2
-            d = d_all[m]
-            w = self.theta[m] + 2.0 * d[None, :] - prep.c[m] / rho
-            if self.capped:
-                pihat, lam = project_capped_simplex(w, prep.q[m])
-            else:
-                pihat, lam = project_simplex(w, prep.q[m])
-            self.theta[m] = pihat - d[None, :]
-            self.lam[m] = lam
-            self.w_hat_m[m] = float(np.sum(prep.c[m] * pihat))
-            self.phat_m[m] = pihat.sum(axis=0)
+            (self.theta[m], self.lam[m], self.w_hat_m[m],
+             self.phat_m[m]) = column_step(self.theta[m], d_all[m], prep.c[m], prep.q[m],
+                                           rho, self.capped)
         for m in Mk:                                          # Step 3
             self.pm[m] = self.theta[m].sum(axis=0)
         self.k += 1
@@ -504,13 +513,16 @@ def unrolled_loss_and_grad(problem, K: int, rho: float, target,
     prep = prepare(problem, "f64")
     M, R, S, a = prep.M, prep.R, prep.S, prep.a
     orc = MamOracle(prep, rho, theta0=theta0)
-    thetas, lams, ds = [], [], []
+    # The reverse pass needs, of each forward step, only its active sets
+    # A_s = {r : w_r > lambda_s}; they are kept as packed bits (one per plan
+    # entry) instead of copies of theta^k.
+    masks = []
     for _ in range(K):
-        thetas.append([t.copy() for t in orc.theta])
         p, _, _ = orc.average()
-        ds.append([(p - orc.pm[m]) / S[m] for m in range(M)])
+        d = [(p - orc.pm[m]) / S[m] for m in range(M)]
+        w = [orc.theta[m] + 2.0 * d[m][None, :] - prep.c[m] / rho for m in range(M)]
         orc.step(diagnostics=False)
-        lams.append([l.copy() for l in orc.lam])
+        masks.append([np.packbits(w[m] > orc.lam[m][:, None], axis=1) for m in range(M)])
     pK = orc.barycenter()
     diff = pK - np.asarray(target, dtype=F64)
     loss = float(np.dot(diff, diff))
@@ -523,8 +535,7 @@ def unrolled_loss_and_grad(problem, K: int, rho: float, target,
         dbar = []
         new_tbar = []
         for m in range(M):
-            w = thetas[k][m] + 2.0 * ds[k][m][None, :] - prep.c[m] / rho
-            A = w > lams[k][m][:, None]
+            A = np.unpackbits(masks[k][m], axis=1, count=R).astype(bool)
             nA = A.sum(axis=1)
             pibar = tbar[m]                                  # theta' = pihat - d
             meanA = np.where(A, pibar, 0.0).sum(axis=1) / nA
