@@ -135,7 +135,6 @@ def nested_ellipses_image(rng, K=60, s_range=(600, 1500), max_tries=10000):
 
 def bezier_strokes_image(rng, K=28, s_range=(80, 250), max_tries=10000):
     """3-6 cubic Bezier strokes, 1.5 px wide, blurred (sigma 0.7 px)."""
-    I, J = _pixel_coords(K)
     t = np.linspace(0.0, 1.0, 200)[:, None]
     for _ in range(max_tries):
         img = np.zeros((K, K))
@@ -143,8 +142,15 @@ def bezier_strokes_image(rng, K=28, s_range=(80, 250), max_tries=10000):
             P = rng.uniform(3, 24, size=(4, 2))
             pts = ((1 - t) ** 3 * P[0] + 3 * (1 - t) ** 2 * t * P[1]
                    + 3 * (1 - t) * t ** 2 * P[2] + t ** 3 * P[3])
-            for pi, pj in pts:
-                img[(I - pi) ** 2 + (J - pj) ** 2 <= 0.75 ** 2] = 1.0
+            # every pixel within 0.75 px of some sample point of the curve; a
+            # pixel that close is one of the 4 around the point
+            i0 = np.floor(pts[:, 0]).astype(np.int64)
+            j0 = np.floor(pts[:, 1]).astype(np.int64)
+            for di in (0, 1):
+                for dj in (0, 1):
+                    ii, jj = i0 + di, j0 + dj
+                    ok = (ii - pts[:, 0]) ** 2 + (jj - pts[:, 1]) ** 2 <= 0.75 ** 2
+                    img[ii[ok], jj[ok]] = 1.0
         img = ndimage.gaussian_filter(img, 0.7)
         img[img < 0.01 * img.max()] = 0.0
         s = int((img > 0).sum())
