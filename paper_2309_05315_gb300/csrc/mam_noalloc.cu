@@ -16,16 +16,20 @@
 #include "mam_handle.h"
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 namespace mam {
 
 constexpr int kNoAllocMaxR = 12288;
 
-// Fixed-point row sums of pi-hat (order-independent integer adds).  Shared
-// by every call on this device: calls whose work overlaps on the GPU race.
-static __device__ __align__(256) unsigned long long g_noalloc_acc[kNoAllocMaxR];
+// Fixed-point row sums of pi-hat (order-independent integer adds) in entries
+// 0..kNoAllocMaxR-1, and one status word after them (0: ok; bit 0: a
+// column's threshold search ended with an empty active set; bit 1: a row sum
+// overflowed the accumulator because mass_bound was below the column masses).
+// Shared by every call on this device: calls whose work overlaps on the GPU
+// race.
+constexpr int kNoAllocStatus = kNoAllocMaxR;
+static __device__ __align__(256) unsigned long long g_noalloc_acc[kNoAllocMaxR + 1];
 
 namespace {
 
@@ -34,6 +38,7 @@ constexpr int kNaThreads = 256;
 __global__ void noalloc_clear(unsigned long long* acc, int R) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
     acc[r] = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) acc[kNoAllocStatus] = 0ull;
 }
 
 // One CTA per column; w lives in shared memory.  Cold start every call:
@@ -72,7 +77,14 @@ __global__ void __launch_bounds__(kNaThreads)
         n += x > 0.f ? 1.f : 0.f;
       }
       reduce3<false>(f, n, z, red, rb, lane, warp, nw);
-      if (n == nprev || n == 0.f) break;
+      if (n == 0.f) {
+        // An empty active set: lambda rounded to or above max w, which
+        // happens only when tau is below the FP32 resolution of w.  The
+        // column would carry no mass, so the call reports a failure.
+        if (tid == 0) atomicOr(acc + kNoAllocStatus, 1ull);
+        break;
+      }
+      if (n == nprev) break;
       nprev = n;
       lam = lam + (f - tau) / n;
     }
@@ -84,15 +96,25 @@ __global__ void __launch_bounds__(kNaThreads)
   }
 }
 
-// rowsum_r = sum_s pihat_rs - S d_r (row sums of theta' = pihat - d).
-__global__ void noalloc_finish(const unsigned long long* acc, const float* d, int R,
-                               int S, double inv_fx, double* out) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
-    out[r] = double((long long)acc[r]) * inv_fx - double(S) * double(d[r]);
+// rowsum_r = sum_s pihat_rs - S d_r (row sums of theta' = pihat - d).  One
+// CTA: every pi-hat entry is >= 0, so a negative signed accumulator means the
+// sum overflowed (mass_bound below the mass of the columns).  A failed column
+// search or an overflow makes every output row NaN, so the caller sees the
+// failure in the one result the call returns.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads)
+    noalloc_finish(unsigned long long* acc, const float* d, int R, int S, double inv_fx,
+                   double* out) {
+  bool ovf = false;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) ovf |= (long long)acc[r] < 0;
+  ovf = __syncthreads_or(ovf) != 0;
+  if (ovf && threadIdx.x == 0) atomicOr(acc + kNoAllocStatus, 2ull);
+  __syncthreads();
+  const bool bad = *(volatile unsigned long long*)(acc + kNoAllocStatus) != 0ull;
+  for (int r = threadIdx.x; r < R; r += blockDim.x)
+    out[r] = bad ? __longlong_as_double(0x7ff8000000000000ll)
+                 : double((long long)acc[r]) * inv_fx - double(S) * double(d[r]);
 }
-
-std::mutex g_mu;
-unsigned long long* g_addr[64] = {nullptr};
 
 }  // namespace
 }  // namespace mam
@@ -116,26 +138,19 @@ extern "C" mam_status mam_column_update_noalloc(float* theta, const float* cost,
     return fail(nullptr, MAM_ERR_INVALID_ARG, "noalloc: rho and mass_bound must be finite and > 0");
   if (size_t(R) * sizeof(float) > 227 * 1024)
     return fail(nullptr, MAM_ERR_INVALID_ARG, "noalloc: column too long");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
-  if (dev < 0 || dev >= 64) return fail(nullptr, MAM_ERR_INVALID_ARG, "noalloc: device id");
-  unsigned long long* acc = nullptr;
-  {
-    // Set-up, once per device (with that device current): the host-side
-    // name of the array is not a device address, so ask for the real one.
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_acc);
-      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
-      e = cudaFuncSetAttribute(noalloc_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(kNoAllocMaxR * sizeof(float)));
-      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
-      g_addr[dev] = static_cast<unsigned long long*>(p);
-    }
-    acc = g_addr[dev];
-  }
+  // Set-up, on every call, with the caller's device current: the host-side
+  // name of the array is not a device address, so ask the runtime for the
+  // real one.  Both calls are host-side lookups; repeating them keeps the
+  // address right if the device's context was reset and the module loaded
+  // again.  The first call on a device also loads the module (lazy loading),
+  // which is why that first call must come before any stream capture.
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_acc);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
+  e = cudaFuncSetAttribute(noalloc_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(kNoAllocMaxR * sizeof(float)));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
+  unsigned long long* acc = static_cast<unsigned long long*>(p);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int e2 = 61 - int(std::ceil(std::log2(mass_bound * 1.0001)));
   const int ex = e2 < 0 ? 0 : (e2 > 100 ? 100 : e2);
@@ -144,7 +159,7 @@ extern "C" mam_status mam_column_update_noalloc(float* theta, const float* cost,
   noalloc_clear<<<gb, 256, 0, st>>>(acc, R);
   noalloc_column<<<S, kNaThreads, size_t(R) * sizeof(float), st>>>(
       theta, cost, q, d, R, ld, float(rho), float(fx), acc);
-  noalloc_finish<<<gb, 256, 0, st>>>(acc, d, R, S, 1.0 / fx, rowsum_out);
+  noalloc_finish<<<1, kFinThreads, 0, st>>>(acc, d, R, S, 1.0 / fx, rowsum_out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "noalloc launch");
   return MAM_OK;

@@ -14,6 +14,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+from oracle.mam_oracle import project_simplex
 from workloads import config1
 
 pytestmark = pytest.mark.gpu
@@ -71,6 +72,85 @@ def test_noalloc_matches_regular_path_twice():
             assert err_th <= TOL, (call, err_th)
             assert err_rows <= TOL, (call, err_rows)
             pm = rows.cpu().numpy()   # the allocation-free chain continues on its own
+
+
+def noalloc_call(L, theta, cost, q, d, R, ld, S, rho, mass_bound, rows):
+    return L.mam_column_update_noalloc(
+        C.c_void_p(theta.data_ptr()), C.c_void_p(cost.data_ptr()), C.c_void_p(q.data_ptr()),
+        C.c_void_p(d.data_ptr()), R, ld, S, float(rho), float(mass_bound),
+        C.c_void_p(rows.data_ptr()), None)
+
+
+def test_noalloc_largest_R_matches_fp64_projection():
+    """R = 12288, the largest column the static accumulator holds (48 KB of
+    dynamic shared memory per CTA): plans and row sums of two calls in a row
+    against FP64 projections of the same FP32 inputs."""
+    torch = pytest.importorskip("torch")
+    from paper_2309_05315_gb300 import _capi
+    from paper_2309_05315_gb300.build import build
+    build()
+    L = _capi.lib()
+    K1, K2 = 96, 128
+    R, S, ld, rho = K1 * K2, 7, K1 * K2 + 8, 40.0
+    i, j = np.meshgrid(np.arange(K1), np.arange(K2), indexing="ij")
+    xi = np.stack([i.ravel() / (K1 - 1), j.ravel() / (K2 - 1)], 1)
+    rng = np.random.default_rng(12)
+    zeta = rng.uniform(size=(S, 2))
+    qh = rng.uniform(0.5, 1.5, size=S).astype(np.float32)
+    qh /= qh.sum()
+    c = np.full((S, ld), np.inf, dtype=np.float32)
+    c[:, :R] = ((zeta[:, None, :] - xi[None, :, :]) ** 2).sum(-1)
+    th = np.zeros((S, ld), dtype=np.float32)
+    th[:, :R] = rng.normal(scale=1e-4, size=(S, R))
+    dh = rng.normal(scale=1e-5, size=R).astype(np.float32)
+    theta = torch.tensor(th, device="cuda")
+    cost = torch.tensor(c, device="cuda")
+    q = torch.tensor(qh, device="cuda")
+    d = torch.tensor(dh, device="cuda")
+    rows = torch.zeros(R, dtype=torch.float64, device="cuda")
+    ref = th[:, :R].astype(np.float64)
+    for call in range(2):
+        _capi.check(noalloc_call(L, theta, cost, q, d, R, ld, S, rho, 1.0, rows))
+        torch.cuda.synchronize()
+        w = ref + 2.0 * dh[None, :].astype(np.float64) - c[:, :R].astype(np.float64) / rho
+        x, _ = project_simplex(w, qh.astype(np.float64))
+        ref = x - dh[None, :].astype(np.float64)
+        got = theta.cpu().numpy()[:, :R].astype(np.float64)
+        for s in range(S):
+            assert np.abs(got[s] - ref[s]).sum() <= TOL * qh[s], (call, s)
+        np.testing.assert_array_equal(theta.cpu().numpy()[:, R:], 0.0)   # padding untouched
+        err_rows = np.abs(rows.cpu().numpy() - ref.sum(axis=0)).sum() / qh.sum()
+        assert err_rows <= TOL, (call, err_rows)
+
+
+def test_noalloc_reports_device_failures_as_nan_rows():
+    """An overflowing accumulator (mass_bound a sixth of the mass that lands
+    on one row) and an empty active set (a weight below the FP32 resolution
+    of w) both make every row sum NaN; a correct call afterwards is clean."""
+    torch = pytest.importorskip("torch")
+    from paper_2309_05315_gb300 import _capi
+    L = _capi.lib()
+    R, S = 64, 4
+    c = np.full((S, R), 50.0, dtype=np.float32)
+    c[:, 0] = 0.0                            # every column wants row 0
+    cost = torch.tensor(c, device="cuda")
+    d = torch.zeros(R, dtype=torch.float32, device="cuda")
+    rows = torch.zeros(R, dtype=torch.float64, device="cuda")
+    q = torch.full((S,), 0.25, dtype=torch.float32, device="cuda")
+    theta = torch.zeros((S, R), dtype=torch.float32, device="cuda")
+    _capi.check(noalloc_call(L, theta, cost, q, d, R, R, S, 1.0, 1.0 / 6.0, rows))
+    torch.cuda.synchronize()
+    assert torch.isnan(rows).all()
+    theta.zero_()
+    _capi.check(noalloc_call(L, theta, cost, q, d, R, R, S, 1.0, 1.0, rows))
+    torch.cuda.synchronize()
+    assert not torch.isnan(rows).any()
+    assert float(rows[0]) == pytest.approx(1.0, abs=1e-6)
+    theta.fill_(1.0)
+    q_tiny = torch.tensor([1e-12, 0.25, 0.25, 0.25], dtype=torch.float32, device="cuda")
+    _capi.check(noalloc_call(L, theta, cost, q_tiny, d, R, R, S, 1.0, 1.0, rows))
+    torch.cuda.synchronize()
+    assert torch.isnan(rows).all()
 
 
 def test_noalloc_rejects_oversized_R():
