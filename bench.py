@@ -1,24 +1,35 @@
 #!/usr/bin/env python3
 """Throughput of the MAM iteration on one GB300 (plan-entry updates / s).
 
-A step is one iteration of Algorithm 1 over every measure of the workload:
-the averaging kernel (Step 1, t^k, Step 3 reduction) and the fused column
-kernel (Step 2 for every plan column).  Default workload: M = 10 seeded
-60x60 nested-ellipse images, R = 3600 grid points, FP32 plans and costs,
-rho = 100 (the paper's untuned value).  The working set (~276 MB per
-iteration) is larger than L2, so no flush is needed between steps.
+A step is one iteration of Algorithm 1: the fused column kernel (Step 2 for
+every plan column of the index set, with the Step 3 row sums) and the
+averaging kernel (Step 3 completion, Step 1 and t^k).  The default workload
+is the largest one that fits one GPU: 100 seeded 100x100 Gaussian-mixture
+images with unequal masses (the unbalanced problem, gamma = 0.01), R = 10000
+grid points, 1.8e9 plan entries, FP32 plans and BF16 costs, 4 bundles of
+Remark 2 (one bundle, about a quarter of the measures, per iteration),
+rho = 100.  Every step streams about 4.4 GB, far more than L2, so no flush
+is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  Under torchrun every rank solves its own
-seeded replica (independent problems, weak scaling, no collective on the
-data path).  ``--impl reference`` times the FP64 oracle on the host cores.
+Prints one JSON line (rank 0).  Besides the headline it carries:
+  nested_ellipses_f32   the same measurement on the 10-measure, R = 3600
+                        nested-ellipse workload with FP32 costs;
+  forms                 the mixed-precision, batched and differentiated forms
+                        against the plain FP32 path on time to a 1e-4 gap;
+  cpu_baseline          the FP64 oracle on the host cores (one thread and
+                        all cores) on a bounded sample of the workload.
+Under torchrun every rank solves its own seeded replica (independent
+problems, weak scaling, no collective on the data path).  ``--impl
+reference`` times the FP64 oracle on the host cores.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -33,28 +44,42 @@ if ROOT not in sys.path:
 METRIC = "MAM plan-entry updates/s"
 UNIT = "plan-entry updates/s"
 FALLBACK_HBM_GBS = 6800.0
+NAMES = {1: "blobs16_M3_R256", 2: "nested_ellipses60_M10_R3600",
+         3: "strokes28_256problems_R784", 4: "mixture40_M8_R1600",
+         5: "mixture100_M100_R10000_unbalanced",
+         6: "nested_ellipses60_M10_free_support_grid_R349281"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 3, 4, 5, 6],
+                    help="1-5: the five synthetic workloads; 6: the nested ellipses on "
+                         "their free-support grid (R = 349281, one cluster per column)")
+    ap.add_argument("--measures", type=int, default=None,
+                    help="keep only the first N measures of each problem (small cases "
+                         "for profiling)")
+    ap.add_argument("--cost-layout", default="per_column", choices=["per_column", "shared"],
+                    help="shared: one cost matrix for measures on a common support")
     ap.add_argument("--cost-dtype", default=None, choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the time-to-gap comparison of the three forms")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the nested-ellipse FP32 line")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--rho", type=float, default=None,
-                    help="rho of the time-to-gap measurement (default: the workload's)")
-    ap.add_argument("--gap-ref-iters", type=int, default=50000)
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: one problem, its measures split over the ranks "
+                         "(mam_create_sharded, NCCL all-reduce of p's partial sums; strong "
+                         "scaling) instead of one replica per rank")
     ap.add_argument("--eta", type=float, default=None,
                     help="capped columns (the full unbalanced extension: projection onto "
                          "Delta_<=(q_s), cost alpha_m (d - eta)) with this eta")
-    ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap measurement")
-    ap.add_argument("--no-diff", action="store_true",
-                    help="mixture workload: skip the forward+backward measurement")
+    ap.add_argument("--gap-ref-iters", type=int, default=50000)
     return ap.parse_args()
 
 
@@ -68,21 +93,36 @@ def workload(idx, rank=0):
         return G.config3(256, i0=256 * rank), "bf16"
     if idx == 4:
         return [G.config4(rank)], "f32"
+    if idx == 6:
+        return [G.config2_free_support(rank)], "f32"
     return [G.config5(rank)], "bf16"
 
 
+def first_measures(probs, n):
+    """The first n measures of each problem (the same images, sizes and
+    costs; for profiling a smaller case of a workload)."""
+    import copy
+    out = []
+    for p in probs:
+        sub = copy.copy(p)
+        k = min(n, p.M)
+        sub.q = list(p.q[:k])
+        sub.zeta = list(p.zeta[:k])
+        sub.alpha = np.full(k, 1.0 / k)
+        if p.n_bundles > k:
+            sub.n_bundles = k
+        out.append(sub)
+    return out
+
+
 def describe(idx, probs, cost_dtype, T, entries):
-    names = {1: "blobs16_M3_R256", 2: "nested_ellipses60_M10_R3600",
-             3: "strokes28_256problems_R784", 4: "mixture40_M8_R1600",
-             5: "mixture100_M100_R10000_unbalanced"}
     p0 = probs[0]
-    cfg = {"workload": names[idx], "problems": len(probs),
-           "measures": int(sum(p.M for p in probs)), "R": p0.R,
-           "kept_columns": int(T), "plan_entries": int(entries),
-           "rho": p0.rho, "gamma": None if np.isinf(p0.gamma) else p0.gamma,
-           "bundles": p0.n_bundles, "cost_dtype": cost_dtype, "theta_dtype": "f32",
-           "parallelism": "replicas (one independent problem per rank)"}
-    return cfg
+    return {"workload": NAMES[idx], "problems": len(probs),
+            "measures": int(sum(p.M for p in probs)), "R": p0.R,
+            "kept_columns": int(T), "plan_entries": int(entries),
+            "rho": p0.rho, "gamma": None if np.isinf(p0.gamma) else p0.gamma,
+            "bundles": p0.n_bundles, "cost_dtype": cost_dtype, "theta_dtype": "f32",
+            "parallelism": "replicas (one independent problem per rank)"}
 
 
 def bytes_per_entry(cost_dtype):
@@ -115,9 +155,10 @@ def kernel_source_hash(kernel="column_kernel"):
 
 
 def ncu_traffic(workload_name, entries, kernel="column_kernel"):
-    """DRAM bytes per column-step launch from the committed ncu summary,
-    scaled to this launch by plan entries; None if there is no record for
-    this workload and kernel, or the kernel's sources changed since."""
+    """DRAM bytes of one column-step launch from the committed ncu record
+    (bytes per plan entry, times the entries of the launch); None if there is
+    no record for this workload and kernel, or the kernel's sources changed
+    since it was taken."""
     path = os.path.join(ROOT, "profiles", "column_kernel_traffic.json")
     try:
         with open(path) as f:
@@ -149,7 +190,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
@@ -180,6 +221,101 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+SHARD = None   # (rank, world) when the problem is measure-sharded over the ranks
+
+
+def make(probs, **kw):
+    from paper_2309_05315_gb300 import Mam
+    if SHARD is not None:
+        from paper_2309_05315_gb300.shard import sharded
+        return sharded(probs[0], SHARD[0], SHARD[1], **kw)
+    return Mam(problems=probs, **kw) if len(probs) > 1 else Mam(probs[0], **kw)
+
+
+def measure(idx, probs, cost_dtype, steps, warmup, local, dist=None, ext=None,
+            autotune=False):
+    """The throughput line of one workload: CUDA events on the library's
+    stream around `steps` graph-replayed iterations (inputs resident), clocks
+    sampled meanwhile, and the column kernel's roofline from a window of
+    individually timed launches after the timed region."""
+    import torch
+    ext = ext or {}
+    # A dedicated (non-default) stream: the library orders its work on it and
+    # the timing events below are recorded on the same stream.
+    stream = torch.cuda.Stream()
+    gpu = make(probs, cost_dtype=cost_dtype, diag="never", stream=stream, **ext)
+    if autotune:
+        gpu.autotune(5)
+    gpu.step(warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = gpu.work()["entries"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gpu.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    time.sleep(0.15)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    entries = gpu.work()["entries"] - w0
+    ms, value = aggregate_ranks(ms, entries / steps, steps, dist, "cuda")
+
+    # Column-kernel duration for the roofline: CUDA events around every
+    # launch on the library's stream (per-launch events keep the kernels from
+    # overlapping, so this window is not the throughput measurement).
+    gpu.profile_enable(True)
+    gpu.profile_read()
+    col_ms = avg_ms = 0.0
+    n_timed = 0
+    win_entries = 0
+    left = max(20, min(steps, 2000))
+    while left > 0:
+        n = min(500, left)
+        w = gpu.work()["entries"]
+        gpu.step(n)
+        left -= n
+        pr = gpu.profile_read()
+        win_entries += gpu.work()["entries"] - w
+        col_ms += pr["column_ms"]
+        avg_ms += pr["average_ms"]
+        n_timed += pr["iterations"]
+    gpu.profile_enable(False)
+    # shared cost layout: the HBM traffic is theta (read and write); the one
+    # cost matrix is read through L2
+    bpe = 8 if ext.get("cost_layout") == "shared" else bytes_per_entry(cost_dtype)
+    peak, peak_kind = peaks()
+    achieved = win_entries * bpe / (col_ms / 1e3) / 1e9
+    alg_launch = win_entries * bpe / max(n_timed, 1)
+    cfg = describe(idx, probs, cost_dtype, gpu.T, gpu.T * gpu.R)
+    cfg.update(ext)
+    cfg["l2"] = (f"inputs larger than L2: {alg_launch / 1e6:.0f} MB of plan/cost traffic per "
+                 "step on average, no flush")
+    cfg["kernel_config"] = gpu.config()
+    kernel = "column_ring_kernel" if cfg["kernel_config"]["kind"] == 1 else "column_kernel"
+    traffic = ncu_traffic(cfg["workload"], win_entries / max(n_timed, 1), kernel)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": kernel, "peak_kind": f"{peak_kind} copy bandwidth",
+            "bytes_per_entry": bpe,
+            "algorithmic_bytes_per_launch": alg_launch,
+            "duration_window": f"{n_timed} launches, one event pair each, after the timed region",
+            "step_achieved_gbs": (entries / steps) * bpe / (ms / steps / 1e3) / 1e9,
+            "avg_launch_ms": col_ms / max(n_timed, 1),
+            "average_kernel_avg_ms": avg_ms / max(n_timed, 1)}
+    gpu.close()
+    del gpu
+    return {"value": value, "ms_per_step": ms / steps, "entries_per_step": entries / steps,
+            "config": cfg, "roofline": roof, "gpu_launches": 2 * steps, "clocks": clocks}
+
+
 def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
                 max_iters=50000, check_every=10, rho=None, ext=None):
     """Time to a 1e-4 objective gap.  The reference W* of each problem comes
@@ -189,18 +325,15 @@ def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
     when balanced, dist_L(pi-hat) / mass <= tol, at two checks in a row; the
     checks (a diagnostic iteration and a host read every check_every
     iterations) are inside the timed wall clock."""
-    import math
     import torch
-    from paper_2309_05315_gb300 import Mam
     kw = dict(cost_dtype=cost_dtype, diag="last", rho=rho, **(ext or {}))
-    make = (lambda: Mam(problems=probs, **kw)) if len(probs) > 1 else (lambda: Mam(probs[0], **kw))
     balanced = [math.isinf(getattr(p, "gamma", math.inf)) for p in probs]
     qa = []
     for p in probs:
         S = np.array([int((np.asarray(q) > 0).sum()) for q in p.q], dtype=float)
         a = (1.0 / S) / (1.0 / S).sum()
         qa.append(float(sum(a[m] * float(np.sum(p.q[m])) for m in range(len(p.q)))))
-    g = make()
+    g = make(probs, **kw)
     wstar = [(-math.inf if b else math.inf) for b in balanced]
     for _ in range(ref_iters // ref_every):
         g.step(ref_every)
@@ -217,7 +350,7 @@ def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
             out.append(gp)
         return max(out)
 
-    g = make()
+    g = make(probs, **kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     it, gap, hits = 0, math.inf, 0
@@ -264,6 +397,70 @@ def forward_backward(prob, K=200, ckpt=20):
             "loss": float(np.sum((p - prob.target) ** 2))}
 
 
+def forms(args):
+    """The three forms against the plain FP32 path on time to a 1e-4 gap
+    (each against the W* of its own problem, so reduced-precision costs are
+    judged on their rounded cost)."""
+    from workloads import generators as G
+    out = {}
+    ell = [G.config2(0)]
+    plain = time_to_gap(ell, "f32", ref_iters=args.gap_ref_iters,
+                        max_iters=args.gap_ref_iters)
+    out["mixed_precision"] = {
+        "workload": NAMES[2] + ", rho = 100",
+        "plain_f32": plain,
+        "bf16_cost": time_to_gap(ell, "bf16", ref_iters=args.gap_ref_iters,
+                                 max_iters=args.gap_ref_iters),
+        "f16_cost": time_to_gap(ell, "f16", ref_iters=args.gap_ref_iters,
+                                max_iters=args.gap_ref_iters)}
+    batch = G.config3(256)
+    rho_b = 10.0
+    sample = batch[:8]
+    single = [time_to_gap([p], "f32", rho=rho_b, ref_iters=args.gap_ref_iters,
+                          max_iters=args.gap_ref_iters) for p in sample]
+    one_s = float(np.mean([r["seconds"] for r in single]))
+    out["batched"] = {
+        "workload": NAMES[3] + f", rho = {rho_b:g}",
+        "batched_bf16": time_to_gap(batch, "bf16", rho=rho_b, ref_iters=args.gap_ref_iters,
+                                    max_iters=args.gap_ref_iters),
+        "plain_f32_one_problem_at_a_time": {
+            "seconds_extrapolated": one_s * len(batch),
+            "sample": f"first {len(sample)} of {len(batch)} problems solved one by one "
+                      "(FP32 cost, single-problem path), mean time to gap x 256",
+            "mean_seconds_per_problem": one_s,
+            "all_reached": all(r["reached"] for r in single),
+            "mean_iterations": float(np.mean([r["iterations"] for r in single]))}}
+    mix = G.config4(0)
+    out["differentiation"] = {
+        "workload": NAMES[4],
+        "forward_backward": forward_backward(mix),
+        "plain_f32_time_to_gap_rho300": time_to_gap([mix], "f32", rho=300.0,
+                                                    ref_iters=args.gap_ref_iters,
+                                                    max_iters=args.gap_ref_iters)}
+    return out
+
+
+def shared_cost_leg(args, local):
+    """The shared cost layout (one cost matrix for measures on a common
+    support; HBM traffic 8 B per entry, the matrix read through L2) against
+    the per-column layout: the stroke batch (one 784 x 784 matrix for all 256
+    problems) and the unbalanced mixtures (one 10000 x 10000 matrix)."""
+    out = {}
+    steps, warm = max(args.steps, 100), max(args.warmup, 10)
+    for idx in (3, 5):
+        probs, dt = workload(idx)
+        sh = measure(idx, probs, dt, steps, warm, local, ext={"cost_layout": "shared"})
+        rec = {"shared": {k: sh[k] for k in ("value", "ms_per_step")},
+               "shared_roofline_frac": sh["roofline"]["frac"],
+               "shared_kernel_config": sh["config"]["kernel_config"]}
+        if idx == 3:
+            pc = measure(idx, probs, dt, steps, warm, local)
+            rec["per_column"] = {k: pc[k] for k in ("value", "ms_per_step")}
+            rec["per_column_roofline_frac"] = pc["roofline"]["frac"]
+        out[NAMES[idx]] = rec
+    return out
+
+
 def aggregate_ranks(ms, units_per_step, steps, dist=None, device="cpu"):
     """Whole-job throughput of independent replicas: the slowest rank's time
     (max over ranks) and the units every rank processed (sum over ranks);
@@ -291,79 +488,103 @@ def extension(args):
     return {} if args.eta is None else {"capped": True, "eta": float(args.eta)}
 
 
-def run_reference(args):
-    """The FP64 oracle on the host cores (reference arm)."""
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return 0
-    from oracle.mam_oracle import MamOracle, prepare
-    probs, cost_dtype = workload(args.workload)
-    prob = probs[0]
-    ext = extension(args)
-    eta, capped = ext.get("eta", 0.0), ext.get("capped", False)
-    prep_full = prepare(prob, eta=eta)
-    T = int(sum(prep_full.S))
-    entries = T * prob.R
-    # Each step is one oracle iteration over a bounded column sample of the
-    # workload, sized so the whole run takes about two minutes.
-    orc_full = MamOracle(prep_full, prob.rho, capped=capped)
-    t0 = time.perf_counter()
-    orc_full.step(diagnostics=False)
-    per_entry = (time.perf_counter() - t0) / entries
-    budget = 120.0
-    n_steps = args.warmup + args.steps
-    cols = int(max(1, min(T, budget / (n_steps * per_entry * prob.R))))
+def oracle_sample(prob, n_measures):
+    """The first n measures of the workload, all their columns (a bounded
+    sample of the same images, sizes and costs)."""
     import copy
-    sub = copy.deepcopy(prob)
-    keep_m = 0
-    idx = np.nonzero(sub.q[keep_m] > 0)[0][:cols]
-    mask = np.zeros_like(sub.q[keep_m])
-    mask[idx] = sub.q[keep_m][idx]
-    sub.q = [mask / mask.sum() * prob.q[keep_m].sum()]
-    sub.zeta = [sub.zeta[keep_m]]
-    sub.alpha = np.array([1.0])
-    orc = MamOracle(prepare(sub, eta=eta), prob.rho, capped=capped)
-    for _ in range(args.warmup):
-        orc.step(diagnostics=False)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        orc.step(diagnostics=False)
-    dt = time.perf_counter() - t0
-    sample_entries = len(idx) * prob.R
-    value = args.steps * sample_entries / dt
-    cfg = describe(args.workload, probs, "f64", T, entries)
-    cfg["theta_dtype"] = "f64"
-    cfg.update(ext)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded images shaped like the paper's workloads)", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(idx)} columns x R={prob.R} of the workload per "
-                                       f"step (numpy FP64 oracle, single thread)"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-    return 0
+    sub = copy.copy(prob)
+    n = min(n_measures, prob.M)
+    sub.q = list(prob.q[:n])
+    sub.zeta = list(prob.zeta[:n])
+    sub.alpha = np.asarray(prob.alpha[:n])
+    if prob.cost is not None:
+        sub.cost = list(prob.cost[:n])
+    return sub
 
 
-def cpu_baseline(prob, entries, seconds=12.0, ext=None):
+def time_oracle(prob, cost_dtype, ext, workers, seconds=None, iters=None, warmup=0):
+    """Oracle iterations on `prob`: one thread (workers = 0, MamOracle) or
+    worker processes (ParallelMamOracle).  Returns (entries/s, iterations,
+    seconds, threads used)."""
     from oracle.mam_oracle import MamOracle, prepare
-    ext = ext or {}
-    prep = prepare(prob, eta=ext.get("eta", 0.0))
-    orc = MamOracle(prep, prob.rho, capped=ext.get("capped", False))
+    from oracle.parallel import ParallelMamOracle
+    eta, capped = ext.get("eta", 0.0), ext.get("capped", False)
+    oc = "f64" if cost_dtype == "f32" else cost_dtype
+    if workers:
+        orc = ParallelMamOracle(prob, prob.rho, capped=capped, cost_dtype=oc, eta=eta,
+                                workers=workers)
+        used = orc.workers
+    else:
+        orc = MamOracle(prepare(prob, oc, eta=eta), prob.rho, capped=capped)
+        used = 1
+    entries = int(sum(int((np.asarray(q) > 0).sum()) for q in prob.q)) * prob.R
+    for _ in range(warmup):
+        orc.step(diagnostics=False)
     n = 0
     t0 = time.perf_counter()
     while True:
         orc.step(diagnostics=False)
         n += 1
-        if time.perf_counter() - t0 >= seconds:
+        dt = time.perf_counter() - t0
+        if (iters is not None and n >= iters) or (iters is None and dt >= seconds):
             break
-    dt = time.perf_counter() - t0
-    return {"value": n * entries / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full oracle iterations of the workload ({dt:.1f} s, numpy FP64, "
-                      f"single thread; host has {os.cpu_count()} cores)"}
+    if workers:
+        orc.close()
+    return n * entries / dt, n, dt, used
+
+
+def cpu_baseline(prob, cost_dtype, ext=None):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the workload: one thread, and one worker process per core."""
+    ext = ext or {}
+    cores = os.cpu_count() or 1
+    one = oracle_sample(prob, 2)
+    v1, n1, t1, _ = time_oracle(one, cost_dtype, ext, 0, seconds=10.0)
+    allc = oracle_sample(prob, cores)
+    va, na, ta, used = time_oracle(allc, cost_dtype, ext, cores, seconds=10.0, warmup=1)
+    return {"value": va, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"the first {allc.M} of {prob.M} measures with all their columns, "
+                      f"{na} iterations in {ta:.1f} s, one worker process per measure group "
+                      f"(numpy FP64; host has {cores} cores)",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"the first {one.M} measures, {n1} iterations in "
+                                        f"{t1:.1f} s, one thread"}}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores (all of them), each
+    step one oracle iteration over a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    probs, cost_dtype = workload(args.workload)
+    if args.measures:
+        probs = first_measures(probs, args.measures)
+    if args.cost_dtype:
+        cost_dtype = args.cost_dtype
+    prob = probs[0]
+    ext = extension(args)
+    cores = os.cpu_count() or 1
+    sample = oracle_sample(prob, cores)
+    value, n, dt, used = time_oracle(sample, cost_dtype, ext, cores, iters=args.steps,
+                                     warmup=args.warmup)
+    T_full = int(sum(int((np.asarray(q) > 0).sum()) for p in probs for q in p.q))
+    cfg = describe(args.workload, probs, cost_dtype, T_full, T_full * prob.R)
+    cfg["theta_dtype"] = "f64"
+    cfg.update(ext)
+    desc = (f"the first {sample.M} of {prob.M} measures of problem 0 with all their columns "
+            f"per step (numpy FP64 oracle, {used} worker processes)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded images shaped like the paper's workloads)", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
 
 
 def main():
@@ -377,127 +598,75 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2309_05315_gb300 import Mam
     from paper_2309_05315_gb300.build import build
     if rank == 0:
         build()
     if dist:
         dist.barrier()
-    probs, cost_dtype = workload(args.workload, rank)
+    global SHARD
+    if args.shard:
+        if len(workload(args.workload, 0)[0]) > 1:
+            raise SystemExit("--shard needs a single-problem workload")
+        SHARD = (rank, ws)
+    # sharded: every rank holds part of problem 0; replicas: rank r solves problem r
+    probs, cost_dtype = workload(args.workload, 0 if args.shard else rank)
+    if args.measures:
+        probs = first_measures(probs, args.measures)
     if args.cost_dtype:
         cost_dtype = args.cost_dtype
-    # A dedicated (non-default) stream: the library orders its work on it and
-    # the timing events below are recorded on the same stream.
-    stream = torch.cuda.Stream()
     ext = extension(args)
-    kw = dict(cost_dtype=cost_dtype, diag="never", stream=stream, **ext)
-    gpu = Mam(problems=probs, **kw) if len(probs) > 1 else Mam(probs[0], **kw)
-    if args.autotune:
-        gpu.autotune(5)
-    entries_per_step = gpu.T * gpu.R
-    if probs[0].n_bundles > 1:  # randomized: expected fraction of columns per step
-        entries_per_step = entries_per_step / probs[0].n_bundles
-    gpu.step(args.warmup)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    time.sleep(0.4)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    # Timed region: the production path (CUDA-graph replay, programmatic
-    # dependent launch between the column and averaging kernels).
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    gpu.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    ms, value = aggregate_ranks(ms, entries_per_step, args.steps, dist, "cuda")
-
-    # Column-kernel duration for the roofline: CUDA events around every
-    # launch on the library's stream, over a window of the same workload run
-    # right after the timed region (per-launch events keep the kernels from
-    # overlapping, so this window is not the throughput measurement).
-    gpu.profile_enable(True)
-    gpu.profile_read()
-    col_ms = avg_ms = 0.0
-    n_timed = 0
-    left = min(args.steps, 4000)
-    while left > 0:
-        n = min(500, left)
-        gpu.step(n)
-        left -= n
-        pr = gpu.profile_read()
-        col_ms += pr["column_ms"]
-        avg_ms += pr["average_ms"]
-        n_timed += pr["iterations"]
-    gpu.profile_enable(False)
-
-    # roofline of the column kernel
-    bpe = bytes_per_entry(cost_dtype)
-    col_avg_s = (col_ms / max(n_timed, 1)) / 1e3
-    alg_bytes = entries_per_step * bpe
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / col_avg_s / 1e9
-    cfg = describe(args.workload, probs, cost_dtype, gpu.T, gpu.T * gpu.R)
-    cfg.update(ext)
-    cfg["l2"] = (f"inputs larger than L2: {alg_bytes / 1e6:.0f} MB of plan/cost traffic per "
-                 "step, no flush")
-    cfg["kernel_config"] = gpu.config()
-    kernel = "column_ring_kernel" if cfg["kernel_config"]["kind"] == 1 else "column_kernel"
-    traffic = ncu_traffic(cfg["workload"], entries_per_step, kernel)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "kernel": kernel, "peak_kind": f"{peak_kind} copy bandwidth",
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "duration_window": f"{n_timed} launches, one event pair each, after the timed region",
-            "step_achieved_gbs": alg_bytes / (ms / args.steps / 1e3) / 1e9,
-            "avg_launch_ms": col_avg_s * 1e3,
-            "average_kernel_avg_ms": avg_ms / max(n_timed, 1)}
-    gpu.close()
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    if args.cost_layout != "per_column":
+        ext["cost_layout"] = args.cost_layout
+    head = measure(args.workload, probs, cost_dtype, args.steps, args.warmup, local, dist,
+                   ext, args.autotune)
+    if args.shard:
+        head["config"]["parallelism"] = (f"measure-sharded over {ws} rank(s): contiguous measure "
+                                         "ranges of equal kept columns, one NCCL all-reduce of "
+                                         "R int64 partial sums of p per iteration (plus 4 FP64 "
+                                         "for t^k)")
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak",
+            "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded images standing in for the "
                                     "paper's datasets)",
-            "config": cfg, "roofline": roof, "gpu_launches": 2 * args.steps,
-            "clocks": clocks}
-
-    if not args.no_gap:
-        line["time_to_gap"] = time_to_gap(probs, cost_dtype, rho=args.rho,
-                                          ref_iters=args.gap_ref_iters,
-                                          max_iters=args.gap_ref_iters, ext=ext)
-    if args.workload == 4 and not args.no_diff and not ext:
-        line["differentiation"] = forward_backward(probs[0])
+            "config": head["config"], "roofline": head["roofline"],
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+            "entries_per_step": head["entries_per_step"]}
 
     if not args.no_e2e:
         # End to end through the public API from host buffers: create (h2d of
         # the problem data), the same number of steps, barycenter (d2h).
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g2 = Mam(problems=probs, cost_dtype=cost_dtype, diag="never", **ext) if len(probs) > 1 \
-            else Mam(probs[0], cost_dtype=cost_dtype, diag="never", **ext)
-        g2.step(args.warmup + args.steps)
+        g2 = make(probs, cost_dtype=cost_dtype, diag="never", **ext)
+        nsteps = args.warmup + args.steps
+        g2.step(nsteps)
         pbar = g2.barycenter()
         dt = time.perf_counter() - t0
+        e2e_entries = g2.work()["entries"]
         g2.close()
-        nsteps = args.warmup + args.steps
         h2d = sum(8 * (sum(len(q) for q in p.q) * (1 + p.dim) + p.M + p.R * p.dim) + 4 * p.M
                   for p in probs)
-        _, e2e_value = aggregate_ranks(dt * 1e3, entries_per_step, nsteps, dist, "cuda")
+        _, e2e_value = aggregate_ranks(dt * 1e3, e2e_entries / nsteps, nsteps, dist, "cuda")
         line["e2e"] = {"value": e2e_value, "unit": UNIT,
                        "h2d_bytes_per_step": h2d / nsteps,
                        "d2h_bytes_per_step": pbar.nbytes / nsteps,
                        "what": f"mam_create from host arrays + {nsteps} mam_step + "
                                "mam_get_barycenter to host, wall clock"}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(probs[0], probs[0].R * int(
-            sum(int((q > 0).sum()) for q in probs[0].q)), ext=ext)
+    SHARD = None
+    if rank == 0 and ws == 1:
+        if not args.no_extra and args.workload != 2:
+            ell, _ = workload(2)
+            x = measure(2, ell, "f32", max(args.steps, 200), max(args.warmup, 10), local)
+            line["nested_ellipses_f32"] = {k: x[k] for k in ("value", "ms_per_step", "config",
+                                                             "roofline", "clocks")}
+        if not args.no_extra and not ext:
+            line["shared_cost"] = shared_cost_leg(args, local)
+        if not args.no_forms:
+            line["forms"] = forms(args)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(probs[0], cost_dtype, ext)
     if rank == 0:
         print(json.dumps(line))
     if dist:

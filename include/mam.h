@@ -59,13 +59,17 @@ typedef enum {
   MAM_ERR_NONFINITE = 4,
   MAM_ERR_TIMEOUT = 5,
   MAM_ERR_STATE = 6,
-  MAM_ERR_UNSUPPORTED = 7
+  MAM_ERR_UNSUPPORTED = 7,
+  MAM_ERR_COMM = 8       /* the exchange callback of a sharded problem failed */
 } mam_status;
 
 /* Storage type of the cost c (theta is always FP32; p, objective and
  * residuals are FP64).  Costs are computed in FP64, rounded to FP32 (nearest)
  * and then, for BF16/F16, rounded again to nearest-even. */
 typedef enum { MAM_F32 = 0, MAM_BF16 = 1, MAM_F16 = 2 } mam_cost_dtype;
+
+/* How the costs are stored (mam_desc.cost_layout). */
+typedef enum { MAM_COST_PER_COLUMN = 0, MAM_COST_SHARED = 1 } mam_cost_layout;
 
 /* When the fused diagnostics (W-hat, dist_L(pi-hat), lower bound, residuals)
  * are computed. */
@@ -121,6 +125,20 @@ typedef struct {
                            column may carry less mass; masses may differ for
                            any gamma.  All problems of a batch share it.
                            Reverse mode needs capped = 0.                    */
+  int32_t cost_layout;  /* 0 (MAM_COST_PER_COLUMN): c^(m) stored column by
+                           column for every kept column (T x R values).
+                           1 (MAM_COST_SHARED): every measure has the same
+                           support points (the same S_m and zeta, before
+                           pruning, as images on one pixel grid have), so
+                           one matrix C_rs = ||xi_r - zeta_s||^2 (- eta when
+                           capped) over that support serves every measure,
+                           and c^(m) = alpha_m C (eq. HugeLP): S x R values
+                           instead of T x R, read from L2 when they fit, and
+                           alpha_m applied in the kernels (to 1/rho).  Needs
+                           the squared Euclidean cost (cost = NULL); in a
+                           batch every problem must have the same support,
+                           xi and eta.  The stored C is rounded to cost_dtype
+                           before alpha_m is applied.                        */
 } mam_desc;
 
 /* Diagnostics of the most recent diagnostic iteration k (all FP64). */
@@ -150,6 +168,56 @@ typedef struct {
  * NULL and nothing is leaked.  Cites: eq. (HugeLP), Section 4.3, Alg. 1
  * Step 0. */
 mam_status mam_create(const mam_desc* desc, mam_problem** out);
+
+/* ---------------------------------------------------------------------
+ * Measure-sharded problems (one problem over several GPUs).
+ *
+ * Step 2 of Algorithm 1 is independent across measures, and Step 1 needs of
+ * them only p = sum_m a_m p^(m) (eq. pr, Prop. 2) and, for t^k, the
+ * distance D^2 = sum_m ||p - p^(m)||^2 / S_m.  A sharded problem gives each
+ * rank a contiguous range of the measures; every iteration the rank runs the
+ * column step on its own columns, forms its partial sum of a_m p^(m) as
+ * 64-bit fixed-point integers and has the caller's callback sum those R
+ * integers over all ranks; the sum is exact, so p (and with it every shift
+ * and every plan) is bit for bit that of the unsharded solver.  When t^k is
+ * needed (gamma finite) or diagnostics are taken, a second exchange sums four
+ * FP64 values (D^2 and diagnostic distances; diagnostic iterations also sum
+ * the R FP64 values of sum_m a_m pi-hat marginals).  Nothing else crosses
+ * ranks.
+ */
+
+/* Exchange callback: sum `count` values of type `dtype` in the device buffer
+ * `buf` over every rank, in place, ordered on the CUDA stream `stream` (a
+ * cudaStream_t): the result must be in `buf` for work enqueued on `stream`
+ * after the call returns.  Return 0 on success.  Every rank calls it the same
+ * number of times with the same counts, in the same order. */
+typedef enum { MAM_SUM_I64 = 0, MAM_SUM_F64 = 1 } mam_sum_dtype;
+typedef int32_t (*mam_allreduce_fn)(void* buf, int64_t count, int32_t dtype, void* stream,
+                                    void* user);
+
+typedef struct {
+  int32_t m_begin;            /* this rank owns measures m_begin .. m_end - 1 */
+  int32_t m_end;              /* of the description (1 <= m_end - m_begin)   */
+  mam_allreduce_fn allreduce; /* required                                    */
+  void* user;                 /* passed to allreduce unchanged               */
+} mam_shard;
+
+/* Create this rank's part of a measure-sharded problem.  `desc` describes
+ * the WHOLE problem (every measure) and must be identical on every rank;
+ * the handle keeps the plans, costs and marginals of measures m_begin ..
+ * m_end - 1 only (the averaging weights a_m, the fixed-point scale and the
+ * bundles of Remark 2 come from all of them).  Collective: every rank calls
+ * it, and it already calls the callback (the Step 0 average).  Afterwards
+ * mam_step, mam_solve and mam_objective are collective too and give the same
+ * p, t and diagnostics on every rank; mam_get_barycenter returns the global
+ * p, mam_get_marginals/mam_get_theta/mam_get_pruned_sizes the rank's own
+ * measures.  Single problem only; no CUDA-graph replay (every iteration
+ * calls the callback); reverse mode and the free-support step are not
+ * offered (MAM_ERR_INVALID_ARG).  A failing callback returns MAM_ERR_COMM and
+ * puts the handle in the error state.  Ranks are usually one per GPU: the
+ * range rule that balances the plan entries is to cut the measures into
+ * contiguous groups of about equal sum_m S_m. */
+mam_status mam_create_sharded(const mam_desc* desc, const mam_shard* shard, mam_problem** out);
 
 /* Batch of n independent problems solved together: every iteration is one
  * launch of the column kernel over all problems' columns plus one averaging
@@ -189,6 +257,19 @@ mam_status mam_get_marginals(mam_problem* h, double* pm_out, int32_t device_ptr)
 /* Current plans, pruned and column-contiguous: [T][R] FP32 where T is the
  * number of kept columns (mam_get_sizes).  Host pointer. */
 mam_status mam_get_theta(mam_problem* h, float* theta_out);
+
+/* Columns col0 .. col0 + ncols - 1 of the current plans (pruned order, as
+ * in mam_get_theta), [ncols][R] FP32, host pointer; synchronises.  For
+ * reading a sample of the columns of a plan too large to copy whole.
+ * MAM_ERR_INVALID_ARG if the range leaves 0..T. */
+mam_status mam_get_theta_range(mam_problem* h, int64_t col0, int64_t ncols, float* theta_out);
+
+/* Work done by the column steps of Step 2 since the handle was created:
+ * plan columns projected and plan entries updated (columns x R), summed
+ * over the index sets M^k actually drawn (Remark 2: a randomized run updates
+ * one bundle per iteration).  Host counters, no synchronisation; either
+ * pointer may be NULL. */
+mam_status mam_get_work(const mam_problem* h, int64_t* columns, int64_t* entries);
 
 /* Sizes: n_problems, total measures, R, kept columns T, padded column
  * stride (floats) of the device plan buffer.  Any pointer may be NULL. */
@@ -250,6 +331,9 @@ mam_status mam_free_support(mam_problem* h, int32_t outer, int32_t inner_iters, 
  *   1, 768 for 2, 512 for 3..4, 192 for 5..6, 384 for 8) x vec float4
  *   groups cover the column; stages (1..4) is the depth of the bulk-copy
  *   pipeline.  Any R up to 12288.
+ * kind 2: one column per thread-block cluster of vec (2, 4, 8, 16) CTAs of
+ *   threads (64..256) threads; each CTA keeps a slice of the column in shared
+ *   memory (columns up to 786432 rows; the default above 12288); stages 1.
  * kind 1: one warp per column.  vec (1,2,4,7,8,13,16) float4 groups
  *   per lane cover the column (R up to 2048; the default for R up to
  *   1024); stages (>= threads/32) is the number of shared-memory ring
@@ -267,8 +351,20 @@ typedef struct {
 mam_status mam_get_config(const mam_problem* h, mam_kernel_config* cfg);
 mam_status mam_set_config(mam_problem* h, const mam_kernel_config* cfg);
 
-/* Time every candidate configuration for `iters` iterations on a copy of the
- * state (the state is restored afterwards) and keep the fastest. */
+/* Autotuner of the column step (the batching form's launch shapes).  Saves
+ * the state, then (1) times every candidate launch shape for `iters`
+ * iterations from that state: one-CTA-per-column shapes (threads x float4
+ * groups covering a column, copy-pipeline depth, resident CTAs per SM, which
+ * fixes the columns each CTA of the persistent grid takes) and
+ * warp-per-column shapes (width, ring slots, warps per CTA, CTAs per SM);
+ * (2) on the fastest shape, times the bisection depths 0, 2, 4, 6, 8, 12,
+ * 16, 24 from the same state with every stored threshold cleared, so that
+ * the first timed iteration takes the cold search (bracket, bisection,
+ * Newton steps; Algorithm 1 Step 2), the only place the depth matters.  The
+ * fastest configuration is kept in the handle and returned in *best (may be
+ * NULL); the state is restored.  On any failure the starting configuration
+ * and state are restored before the status is returned.  Synchronises.  Not
+ * offered for sharded problems (MAM_ERR_INVALID_ARG). */
 mam_status mam_autotune(mam_problem* h, int32_t iters, mam_kernel_config* best);
 
 /* Measurement support: while enabled, every iteration is launched on its own
@@ -293,14 +389,20 @@ mam_status mam_profile_read(mam_problem* h, double* column_ms, double* average_m
  * rowsum_out [R].  mass_bound must be >= sum_s q_s (it fixes the scale of
  * the integer accumulator).  Work is enqueued on `stream` (NULL = default
  * stream); the call does not synchronise.
- * Scratch: a file-scope device array of 12288 64-bit integers (96 KB) that
- * every GPU loading the library keeps until exit; R > 12288 is rejected with
- * MAM_ERR_INVALID_ARG.  The array is cleared at the start of every call, and
- * all calls on a device share it, so calls whose work overlaps on the GPU
- * (different streams, concurrently) race and give wrong row sums.  The first
- * call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Errors go to
- * mam_last_error(NULL). */
+ * Failures on the device: the call's only result is rowsum_out, so a column
+ * whose threshold search ends with an empty active set (q_s below the FP32
+ * resolution of w) or a row sum that overflows the accumulator (mass_bound
+ * too small: overflow needs about 4x the true mass and is detected up to
+ * about 8x) makes every rowsum_out entry NaN.
+ * Scratch: a file-scope device array of 12288 64-bit integers plus one
+ * status word (96 KB) that every GPU loading the library keeps until exit;
+ * R > 12288 is rejected with MAM_ERR_INVALID_ARG.  The array is cleared at
+ * the start of every call, and all calls on a device share it, so calls
+ * whose work overlaps on the GPU (different streams, concurrently) race and
+ * give wrong row sums.  Every call looks up the array's device address with
+ * the caller's device current (a host-side lookup); the first call on a
+ * device also loads the library's device code, so make that first call
+ * before any stream capture.  Errors go to mam_last_error(NULL). */
 mam_status mam_column_update_noalloc(float* theta, const float* cost, const float* q,
                                      const float* d, int32_t R, int32_t ld, int32_t S,
                                      double rho, double mass_bound, double* rowsum_out,

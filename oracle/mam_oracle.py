@@ -192,7 +192,8 @@ def sq_euclid_cost(xi, zeta, alpha_m, eta: float = 0.0):
     return alpha_m * (np.einsum("srd,srd->sr", diff, diff) - eta)
 
 
-def prepare(problem, cost_dtype: str = "f64", eta: float = 0.0) -> Prepared:
+def prepare(problem, cost_dtype: str = "f64", eta: float = 0.0,
+            round_before_alpha: bool = False) -> Prepared:
     """Drop zero-weight columns (Section 4.3) and build the costs.
 
     The cost of measure m is alpha_m ||xi_r - zeta_s||^2 (eq. HugeLP), or
@@ -202,6 +203,9 @@ def prepare(problem, cost_dtype: str = "f64", eta: float = 0.0) -> Prepared:
     alpha_m (||xi_r - zeta_s||^2 - eta), or alpha_m (C^(m) - eta).
     ``cost_dtype`` in {"f64", "f32", "bf16", "f16"} rounds the stored cost
     the way a reduced-precision store would (FP64 -> FP32 -> target).
+    ``round_before_alpha`` rounds the distance matrix before alpha_m scales
+    it (a store that keeps one matrix for all measures and applies alpha_m
+    afterwards); by default the scaled cost alpha_m d is rounded.
     """
     xi = np.asarray(problem.xi, dtype=F64)
     S, keep, qs, zs, cs = [], [], [], [], []
@@ -212,10 +216,12 @@ def prepare(problem, cost_dtype: str = "f64", eta: float = 0.0) -> Prepared:
         qs.append(qm[idx])
         zs.append(np.asarray(problem.zeta[m], dtype=F64)[idx])
         S.append(len(idx))
+        am = float(problem.alpha[m])
+        scale = 1.0 if round_before_alpha else am
         if problem.cost is not None:
-            cm = problem.alpha[m] * (np.asarray(problem.cost[m], dtype=F64)[idx] - eta)
+            cm = scale * (np.asarray(problem.cost[m], dtype=F64)[idx] - eta)
         else:
-            cm = sq_euclid_cost(xi, zs[-1], float(problem.alpha[m]), eta)
+            cm = sq_euclid_cost(xi, zs[-1], scale, eta)
         if cost_dtype == "f32":
             cm = cm.astype(np.float32).astype(F64)
         elif cost_dtype == "bf16":
@@ -224,7 +230,7 @@ def prepare(problem, cost_dtype: str = "f64", eta: float = 0.0) -> Prepared:
             cm = round_to_f16(cm)
         elif cost_dtype != "f64":
             raise ValueError(cost_dtype)
-        cs.append(cm)
+        cs.append(am * cm if round_before_alpha else cm)
     S = np.asarray(S, dtype=np.int64)
     return Prepared(R=xi.shape[0], S=S, keep=keep, q=qs, zeta=zs, xi=xi,
                     alpha=np.asarray(problem.alpha, dtype=F64), c=cs,

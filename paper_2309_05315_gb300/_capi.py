@@ -15,9 +15,10 @@ LIB_PATH = os.path.join(_PKG, "libmam.so")
 MAM_OK = 0
 STATUS = {0: "MAM_OK", 1: "MAM_ERR_INVALID_ARG", 2: "MAM_ERR_CUDA", 3: "MAM_ERR_OOM",
           4: "MAM_ERR_NONFINITE", 5: "MAM_ERR_TIMEOUT", 6: "MAM_ERR_STATE",
-          7: "MAM_ERR_UNSUPPORTED"}
+          7: "MAM_ERR_UNSUPPORTED", 8: "MAM_ERR_COMM"}
 COST_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 DIAG_MODES = {"last": 0, "never": 1, "every": 2}
+COST_LAYOUTS = {"per_column": 0, "shared": 1}
 
 
 class MamDesc(C.Structure):
@@ -32,7 +33,19 @@ class MamDesc(C.Structure):
                 ("n_bundles", C.c_int32), ("seed", C.c_uint64),
                 ("cost_dtype", C.c_int32), ("theta0_mode", C.c_int32),
                 ("diag_mode", C.c_int32), ("stream", C.c_void_p),
-                ("eta", C.c_double), ("capped", C.c_int32)]
+                ("eta", C.c_double), ("capped", C.c_int32),
+                ("cost_layout", C.c_int32)]
+
+
+# int32 allreduce(void* buf, int64 count, int32 dtype, void* stream, void* user)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                           C.c_void_p)
+SUM_I64, SUM_F64 = 0, 1
+
+
+class MamShard(C.Structure):
+    _fields_ = [("m_begin", C.c_int32), ("m_end", C.c_int32),
+                ("allreduce", ALLREDUCE_FN), ("user", C.c_void_p)]
 
 
 class MamObjective(C.Structure):
@@ -78,7 +91,11 @@ _SIGS = {
     "mam_free_support": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32,
                                    C.c_void_p, C.c_void_p]),
     "mam_selftest_wait_timeout": (C.c_int, [C.c_int32]),
+    "mam_create_sharded": (C.c_int, [C.POINTER(MamDesc), C.POINTER(MamShard),
+                                     C.POINTER(C.c_void_p)]),
     "mam_get_theta": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mam_get_theta_range": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]),
+    "mam_get_work": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mam_get_marginals": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "mam_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int64),

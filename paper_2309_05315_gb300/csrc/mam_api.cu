@@ -9,8 +9,10 @@
 #include "mam_internal.h"
 #include "mam_support.h"
 #include "mam_handle.h"
+#include "mam_device.cuh"
 
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,7 +28,7 @@ thread_local std::string g_last_error;
 mam_status fail(mam_problem* h, mam_status code, const std::string& msg) {
   if (h) {
     h->err = msg;
-    if (code == MAM_ERR_CUDA || code == MAM_ERR_TIMEOUT) h->failed = true;
+    if (code == MAM_ERR_CUDA || code == MAM_ERR_TIMEOUT || code == MAM_ERR_COMM) h->failed = true;
   } else {
     g_last_error = msg;
   }
@@ -55,18 +57,6 @@ size_t cost_elem_size(int dt) { return dt == MAM_F32 ? 4 : 2; }
 
 }  // namespace mam
 
-#define MAM_TRY(x)                     \
-  do {                                 \
-    mam_status _s = (x);               \
-    if (_s != MAM_OK) return _s;       \
-  } while (0)
-
-#define MAM_CUDA(x, where)                                \
-  do {                                                    \
-    cudaError_t _e = (x);                                 \
-    if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
-  } while (0)
-
 namespace {
 
 bool finite_all(const double* v, size_t n) {
@@ -83,7 +73,7 @@ mam_status validate(const mam_desc* d, int idx) {
   if (d->R > kMaxR)
     return fail(nullptr, MAM_ERR_INVALID_ARG,
                 p + "R must be <= " + std::to_string(kMaxR) +
-                    " (one CTA holds a whole column in registers)");
+                    " (a cluster of 16 CTAs holds a whole column in shared memory)");
   if (d->dim < 1 || d->dim > 3)
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "dim must be 1..3");
   if (!d->S || !d->q || !d->alpha || !d->xi)
@@ -110,11 +100,30 @@ mam_status validate(const mam_desc* d, int idx) {
   if (!std::isfinite(d->eta) || d->eta < 0 || (!d->capped && d->eta != 0))
     return fail(nullptr, MAM_ERR_INVALID_ARG,
                 p + "eta must be finite and >= 0, and 0 unless capped is set");
+  if (d->cost_layout != MAM_COST_PER_COLUMN && d->cost_layout != MAM_COST_SHARED)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "unknown cost_layout");
   long long tot = 0;
   for (int m = 0; m < d->M; ++m) {
     if (d->S[m] < 1)
       return fail(nullptr, MAM_ERR_INVALID_ARG, p + "every S_m must be >= 1");
     tot += d->S[m];
+  }
+  if (d->cost_layout == MAM_COST_SHARED) {
+    // one support for every measure: the same S_m and the same points
+    if (d->cost || !d->zeta)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  p + "the shared cost layout needs support points and the squared "
+                      "Euclidean cost (cost = NULL)");
+    for (int m = 1; m < d->M; ++m) {
+      if (d->S[m] != d->S[0])
+        return fail(nullptr, MAM_ERR_INVALID_ARG,
+                    p + "the shared cost layout needs the same support for every measure");
+      const size_t n = size_t(d->S[0]) * d->dim;
+      if (std::memcmp(d->zeta, d->zeta + size_t(m) * n, n * sizeof(double)) != 0)
+        return fail(nullptr, MAM_ERR_INVALID_ARG,
+                    p + "the shared cost layout needs the same support points for every "
+                        "measure");
+    }
   }
   if (!finite_all(d->q, size_t(tot)) || !finite_all(d->alpha, size_t(d->M)) ||
       !finite_all(d->xi, size_t(d->R) * d->dim) ||
@@ -189,6 +198,23 @@ size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c) {
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
+  if (c.kind == 2) {  // one column per thread-block cluster
+    if (c.vec != 2 && c.vec != 4 && c.vec != 8 && c.vec != 16)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "kind 2: vec (CTAs per cluster) must be 2, 4, 8 or 16");
+    if (c.threads < 64 || c.threads % 32 || c.threads > 256)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "kind 2: threads must be a multiple of 32 in 64..256");
+    if (c.stages != 1)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "kind 2: stages must be 1");
+    if (cluster_kernel_smem(h->ld, c.vec) > 196608)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                  "kind 2: a CTA's slice of the column exceeds 192 KB; use more CTAs per "
+                  "cluster");
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32 || c.bisect_depth < 0 || c.bisect_depth > 30)
+      return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "bad ctas_per_sm or bisect_depth");
+    return MAM_OK;
+  }
   if (c.kind == 1) {  // one warp per column, shared-memory ring
     if (!ring_kernel_has(c.vec))
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
@@ -212,7 +238,7 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
     return MAM_OK;
   }
   if (c.kind != 0)
-    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "kind must be 0 or 1");
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG, "kind must be 0, 1 or 2");
   const int nvs[] = {1, 2, 3, 4, 5, 6, 8};
   if (std::find(std::begin(nvs), std::end(nvs), c.vec) == std::end(nvs))
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
@@ -245,6 +271,23 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
 // for the ring kernel; R = 3600: 54 us against 81 us).
 mam_kernel_config default_config(const mam_problem* h) {
   const int ld4 = h->ld / 4;
+  if (h->ld > kMaxCtaR) {
+    // Longer than one CTA holds: a cluster per column, the fewest CTAs whose
+    // slices stay within 64 KB of w (several resident CTAs per SM), else 16.
+    mam_kernel_config c{};
+    c.kind = 2;
+    c.vec = 16;
+    for (int cs : {2, 4, 8, 16})
+      if (cluster_kernel_smem(h->ld, cs) <= 65536) {
+        c.vec = cs;
+        break;
+      }
+    c.threads = 256;
+    c.stages = 1;
+    c.ctas_per_sm = 0;
+    c.bisect_depth = 4;
+    return c;
+  }
   if (h->ld <= 1024) {
     // The narrowest compiled width that covers the column, up to 12 ring
     // slots (as many as fit in shared memory) and one warp per slot.
@@ -313,6 +356,43 @@ mam_kernel_config default_config(const mam_problem* h) {
 
 mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
   MAM_TRY(check_config(h, c));
+  if (c.kind == 2) {
+    const size_t smem = cluster_kernel_smem(h->ld, c.vec);
+    int clusters = 1 << 30;
+    for (int dg = 0; dg < 2; ++dg) {
+      MAM_CUDA(set_column_cluster_smem(h->cost_dtype, dg != 0, smem), "cudaFuncSetAttribute");
+      int n = 0;
+      MAM_CUDA(column_cluster_occupancy(h->cost_dtype, dg != 0, c.vec, c.threads, smem, &n),
+               "cluster occupancy");
+      clusters = std::min(clusters, n);
+    }
+    if (clusters < 1)
+      return fail(h, MAM_ERR_INVALID_ARG, "cluster configuration cannot be resident");
+    if (c.ctas_per_sm > 0)  // at most ctas_per_sm CTAs of this kernel per SM
+      clusters = std::min<long long>(clusters, (long long)c.ctas_per_sm * h->num_sms / c.vec);
+    long long max_cols = 0;
+    for (auto& r : h->index_sets) max_cols = std::max(max_cols, r.second - r.first);
+    const long long G = std::max(1LL, std::min<long long>(clusters, max_cols));
+    free_sched(h);
+    std::vector<Sched> sd(h->index_sets.size());
+    for (size_t i = 0; i < sd.size(); ++i) {
+      sd[i].col_begin = h->index_sets[i].first;
+      sd[i].col_end = h->index_sets[i].second;
+      sd[i].meas_begin = h->index_meas[i].first;
+      sd[i].meas_end = h->index_meas[i].second;
+    }
+    void* sp;
+    MAM_TRY(sched_alloc(h, &sp, sd.size() * sizeof(Sched)));
+    MAM_CUDA(cudaMemcpyAsync(sp, sd.data(), sd.size() * sizeof(Sched), cudaMemcpyHostToDevice,
+                             h->stream),
+             "sched upload");
+    h->sched_d = static_cast<Sched*>(sp);
+    h->cfg = c;
+    h->grid = int(G * c.vec);
+    h->smem = smem;
+    MAM_CUDA(cudaStreamSynchronize(h->stream), "schedule upload");
+    return MAM_OK;
+  }
   const bool wk = c.kind == 1;
   const size_t smem = wk ? ring_kernel_smem(c.vec, c.stages, int(cost_elem_size(h->cost_dtype)))
                          : column_smem_bytes(h, c);
@@ -370,6 +450,8 @@ ColArgs col_args(const mam_problem* h) {
   ColArgs a{};
   a.theta = h->theta;
   a.cost = h->cost;
+  a.cost_col = h->cost_col;
+  a.cmul = h->cmul;
   a.q = h->q;
   a.lam = h->lam;
   a.nact = h->nact;
@@ -378,8 +460,8 @@ ColArgs col_args(const mam_problem* h) {
   a.delta32 = h->delta32;
   a.amask = h->amask;
   a.mw = (h->ld + 31) / 32;
-  a.blk = h->blk;
-  a.nblk = avg_blocks(h);
+  a.blk = h->sharded ? h->blk_glob : h->blk;  // sharded: the global sums, one block
+  a.nblk = h->sharded ? 1 : avg_blocks(h);
   a.rho_p = h->rho_d;
   a.gamma_p = h->gamma_d;
   a.t_used = h->t_used;
@@ -474,7 +556,10 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
     MAM_CUDA(cudaEventRecord(ev[0], h->stream), "cudaEventRecord");
   }
   const ColArgs ca = col_args(h);
-  MAM_CUDA(h->cfg.kind == 1
+  MAM_CUDA(h->cfg.kind == 2
+               ? launch_column_cluster(h->cost_dtype, diag, h->cfg.vec, h->grid,
+                                       h->cfg.threads, h->smem, h->stream, ca)
+           : h->cfg.kind == 1
                ? launch_column_ring(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
                                     h->smem, h->stream, ca)
                : launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
@@ -483,15 +568,20 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
   if (diag && h->nb > 1) {
     // Lower bound of every measure for the v^k the column step just used
     // (the fused value covers only the drawn bundle).
-    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->q, h->delta32, h->t_used, h->meas_prob,
+    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->cost_col, h->cmul, h->q, h->delta32,
+                       h->t_used, h->meas_prob,
                        h->rho_m, h->col_meas, h->T, h->R, h->ld,
                        h->capped ? 0.f : INFINITY, h->diag_lb,
                        h->stream),
              "lower-bound kernel");
   }
   if (h->profiling) MAM_CUDA(cudaEventRecord(ev[1], h->stream), "cudaEventRecord");
-  const AvgArgs aa = avg_args(h, 1, diag ? 1 : 0);
-  MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
+  if (h->sharded) {
+    MAM_TRY(shard_average(h, 1, diag));
+  } else {
+    const AvgArgs aa = avg_args(h, 1, diag ? 1 : 0);
+    MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
+  }
   if (h->profiling) MAM_CUDA(cudaEventRecord(ev[2], h->stream), "cudaEventRecord");
   return MAM_OK;
 }
@@ -518,16 +608,38 @@ static mam_status ensure_graph(mam_problem* h) {
   return MAM_OK;
 }
 
+// Columns of the index sets of column steps k0 .. k0 + n - 1 (the host
+// evaluates the same counter-based draw as the kernels).
+static long long drawn_columns(const mam_problem* h, long long k0, int n) {
+  if (h->nb <= 1) return (long long)n * (h->index_sets[0].second - h->index_sets[0].first);
+  Draw d = draw_args(h);
+  d.cum = h->bundle_cum.data();
+  long long cols = 0;
+  for (long long k = k0; k < k0 + n; ++k) {
+    const auto& r = h->index_sets[draw_index_set(d, k)];
+    cols += r.second - r.first;
+  }
+  return cols;
+}
+
 mam_status run_iterations(mam_problem* h, int n, bool diag_last) {
   if (n <= 0) return MAM_OK;
+  {
+    const long long cols = drawn_columns(h, h->iter, n);
+    h->work_cols += cols;
+    h->work_entries += cols * h->R;
+  }
   const bool every = h->diag_mode == MAM_DIAG_EVERY;
   const int nd = every ? n : (diag_last ? 1 : 0);
   int plain = n - nd;
-  if (h->profiling) {  // per-kernel events need individual launches
+  if (h->profiling || h->sharded) {  // per-kernel events / the exchange callback
+    // need individual launches
     while (plain-- > 0) MAM_TRY(launch_iteration(h, false));
     plain = 0;
   }
-  if (plain >= kGraphIters) MAM_TRY(ensure_graph(h));
+  // The graph is captured on the first call that has plain iterations, so
+  // that a later call of kGraphIters or more does not pay the capture.
+  if (plain > 0) MAM_TRY(ensure_graph(h));
   while (plain >= kGraphIters) {
     MAM_CUDA(cudaGraphLaunch(h->graph, h->stream), "cudaGraphLaunch");
     plain -= kGraphIters;
@@ -576,18 +688,32 @@ mam_status reset_state(mam_problem* h) {
   MAM_CUDA(cudaMemsetAsync(h->blk, 0, sizeof(double) * 4 * h->P * avg_blocks(h), h->stream), "memset");
   std::vector<double> ones(h->P, 1.0);
   MAM_TRY(upload(h, h->t_used, ones.data(), ones.size()));
-  const AvgArgs aa = avg_args(h, 0, 0);
-  MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
+  if (h->sharded) {
+    MAM_CUDA(cudaMemsetAsync(h->blk_glob, 0, sizeof(double) * 4, h->stream), "memset");
+    MAM_TRY(shard_average(h, 0, false));
+  } else {
+    const AvgArgs aa = avg_args(h, 0, 0);
+    MAM_CUDA(launch_average(aa, avg_blocks(h), h->stream), "average kernel launch");
+  }
   h->iter = 0;
   h->diag_iter = -1;
   return sync(h);
 }
 
-static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
+static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
+                              const mam_shard* shard = nullptr) {
   if (!out) return fail(nullptr, MAM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || !descs) return fail(nullptr, MAM_ERR_INVALID_ARG, "need at least one problem");
   for (int i = 0; i < n; ++i) MAM_TRY(validate(&descs[i], i));
+  if (shard) {
+    if (n != 1) return fail(nullptr, MAM_ERR_INVALID_ARG, "a sharded problem is a single problem");
+    if (!shard->allreduce)
+      return fail(nullptr, MAM_ERR_INVALID_ARG, "sharded problem: allreduce callback is NULL");
+    if (shard->m_begin < 0 || shard->m_end > descs[0].M || shard->m_end <= shard->m_begin)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  "sharded problem: need 0 <= m_begin < m_end <= M");
+  }
   for (int i = 1; i < n; ++i) {
     if (descs[i].R != descs[0].R || descs[i].dim != descs[0].dim ||
         descs[i].cost_dtype != descs[0].cost_dtype ||
@@ -596,6 +722,18 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
       return fail(nullptr, MAM_ERR_INVALID_ARG,
                   "batched problems must share R, dim, cost_dtype, diag_mode, theta0_mode "
                   "and capped");
+    if (descs[i].cost_layout != descs[0].cost_layout)
+      return fail(nullptr, MAM_ERR_INVALID_ARG, "batched problems must share cost_layout");
+    if (descs[0].cost_layout == MAM_COST_SHARED) {
+      const size_t nx = size_t(descs[0].R) * descs[0].dim;
+      const size_t nz = size_t(descs[0].S[0]) * descs[0].dim;
+      if (descs[i].S[0] != descs[0].S[0] || descs[i].eta != descs[0].eta ||
+          std::memcmp(descs[i].xi, descs[0].xi, nx * sizeof(double)) != 0 ||
+          std::memcmp(descs[i].zeta, descs[0].zeta, nz * sizeof(double)) != 0)
+        return fail(nullptr, MAM_ERR_INVALID_ARG,
+                    "a batch with the shared cost layout needs the same support points, "
+                    "xi and eta in every problem");
+    }
   }
   if (n > 1)
     for (int i = 0; i < n; ++i)
@@ -604,6 +742,17 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
                     "batched problems must be deterministic (n_bundles <= 1)");
 
   mam_problem* h = new mam_problem();
+  // measures kept by this handle: all (every problem of a batch), or a
+  // sharded rank's range of the single problem
+  const int mb = shard ? shard->m_begin : 0;
+  const int me = shard ? shard->m_end : std::numeric_limits<int>::max();
+  if (shard) {
+    h->sharded = true;
+    h->m_begin = mb;
+    h->M_global = descs[0].M;
+    h->allreduce = shard->allreduce;
+    h->ar_user = shard->user;
+  }
   auto bail = [&](mam_status s) {
     if (h->failed || s != MAM_OK) g_last_error = h->err;
     mam_destroy(h);
@@ -618,6 +767,8 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   h->capped = d0.capped != 0;
   h->theta0_mode = d0.theta0_mode;
   h->diag_mode = d0.diag_mode;
+  h->shared_cost = d0.cost_layout == MAM_COST_SHARED;
+  h->n_sup = h->shared_cost ? d0.S[0] : 0;
   h->nb = (n == 1 && d0.n_bundles > 1) ? d0.n_bundles : 1;
   h->seed = d0.seed;
   cudaError_t e = cudaGetDevice(&h->device);
@@ -642,6 +793,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   std::vector<int> col_meas;
   std::vector<double> alpha_m, eta_m;
   long long uoff_global = 0;
+  double qmax = 0;  // largest kept mass over every measure (all ranks' too)
   for (int i = 0; i < n; ++i) {
     const mam_desc& d = descs[i];
     double inv_sum = 0;
@@ -649,15 +801,29 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
     long long uoff = 0;
     for (int m = 0; m < d.M; ++m) {
       int cnt = 0;
-      for (int s = 0; s < d.S[m]; ++s) cnt += d.q[uoff + s] > 0;
+      double Q = 0;
+      for (int s = 0; s < d.S[m]; ++s) {
+        cnt += d.q[uoff + s] > 0;
+        if (d.q[uoff + s] > 0) Q += d.q[uoff + s];
+      }
       Sp[m] = cnt;
       inv_sum += 1.0 / cnt;
+      qmax = std::max(qmax, Q);
       uoff += d.S[m];
     }
     uoff = 0;
     double Qa = 0;
+    int local = 0;
     for (int m = 0; m < d.M; ++m) {
-      const int gm = h->Mtot + m;
+      if (m < mb || m >= me) {  // another rank's measure: only its mass enters Qa
+        double Q = 0;
+        for (int s = 0; s < d.S[m]; ++s)
+          if (d.q[uoff + s] > 0) Q += d.q[uoff + s];
+        Qa += (1.0 / Sp[m]) / inv_sum * Q;
+        uoff += d.S[m];
+        continue;
+      }
+      const int gm = h->Mtot + local++;
       h->S.push_back(Sp[m]);
       h->S_unpruned.push_back(d.S[m]);
       const double am = (1.0 / Sp[m]) / inv_sum;
@@ -684,7 +850,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
       uoff += d.S[m];
     }
     uoff_global += uoff;
-    h->Mtot += d.M;
+    h->Mtot += local;
     h->prob_meas.push_back(h->Mtot);
     h->prob_cols.push_back(h->col_off.back());
     h->rho.push_back(d.rho);
@@ -695,7 +861,9 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   if (h->T >= (1LL << 31) - 1)
     return bail(fail(h, MAM_ERR_INVALID_ARG, "too many kept columns (>= 2^31)"));
 
-  // Index sets: all columns, or the bundles of Remark 2 (contiguous measures).
+  // Index sets: all columns, or the bundles of Remark 2 (contiguous measures
+  // of the whole problem; a sharded rank keeps the part it owns, possibly
+  // none).
   if (h->nb > 1) {
     const int M = d0.M;
     double tot = 0;
@@ -706,8 +874,10 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
       for (int m = m0; m < m1; ++m) s += d0.alpha[m];
       beta[b] = s;
       tot += s;
-      h->index_sets.push_back({h->col_off[m0], h->col_off[m1]});
-      h->index_meas.push_back({m0, m1});
+      const int l0 = std::min(std::max(m0, mb), std::min(me, M)) - mb;
+      const int l1 = std::min(std::max(m1, mb), std::min(me, M)) - mb;
+      h->index_sets.push_back({h->col_off[l0], h->col_off[l1]});
+      h->index_meas.push_back({l0, l1});
     }
     if (!(tot > 0))
       return bail(fail(h, MAM_ERR_INVALID_ARG, "randomized MAM needs sum(alpha) > 0"));
@@ -724,12 +894,6 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   // a row is at most the measure's mass, so Qmax * 2^e <= 2^61 cannot
   // overflow the signed 64-bit accumulators.
   {
-    double qmax = 0;
-    for (int m = 0; m < h->Mtot; ++m) {
-      double Q = 0;
-      for (long long c = h->col_off[m]; c < h->col_off[m + 1]; ++c) Q += q64[c];
-      qmax = std::max(qmax, Q);
-    }
     // 2 bits of headroom over the largest mass: the marginals p^(m) (row
     // sums of theta = pihat - d) and p are held in the same fixed point.
     int e2 = 59 - int(std::ceil(std::log2(qmax * 1.0001)));
@@ -746,8 +910,9 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->theta, Tld, "plans theta");
   void* costp = nullptr;
   {
+    const size_t ncost = h->shared_cost ? size_t(h->n_sup) * h->ld : Tld;
     char* cp = nullptr;
-    ALLOC(cp, Tld * cost_elem_size(h->cost_dtype), "costs");
+    ALLOC(cp, ncost * cost_elem_size(h->cost_dtype), "costs");
     costp = cp;
   }
   h->cost = costp;
@@ -790,12 +955,59 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
   ALLOC(h->col_meas, size_t(h->T), "column table");
   ALLOC(h->bundle_cum_d, std::max<size_t>(1, h->bundle_cum.size()), "bundle table");
   ALLOC(h->iter_d, 1, "iteration counter");
+  ALLOC(h->cmul, size_t(h->Mtot), "cost factors");
+  if (h->shared_cost) {
+    ALLOC(h->cost_col, size_t(h->T), "cost columns");
+    ALLOC(h->sup_zeta_d, size_t(h->n_sup) * h->dim, "support points");
+    ALLOC(h->sup_meas_d, size_t(h->n_sup), "support table");
+    ALLOC(h->sup_alpha_d, 1, "support weight");
+    ALLOC(h->sup_eta_d, 1, "support eta");
+  }
+  if (h->sharded) {
+    ALLOC(h->exch_i64, size_t(h->R), "exchange buffer");
+    ALLOC(h->exch_f64, size_t(h->R), "exchange buffer");
+    ALLOC(h->blk_glob, 4, "global block sums");
+  }
 #undef ALLOC
 
-  std::vector<float> rho_m(h->Mtot), irho_m(h->Mtot);
+  // Shared cost: the stored matrix is C, so alpha_m goes into the factor of
+  // c in w = theta + 2 d - c / rho (and into the diagnostics' cost factor).
+  std::vector<float> rho_m(h->Mtot), irho_m(h->Mtot), cmul(h->Mtot, 1.f);
   for (int m = 0; m < h->Mtot; ++m) {
     rho_m[m] = float(h->rho[h->meas_prob_h[m]]);
-    irho_m[m] = float(1.0 / h->rho[h->meas_prob_h[m]]);
+    const double a = h->shared_cost ? alpha_m[m] : 1.0;
+    irho_m[m] = float(a / h->rho[h->meas_prob_h[m]]);
+    cmul[m] = float(a);
+  }
+  if ((s = upload(h, h->cmul, cmul.data(), cmul.size())) != MAM_OK) return bail(s);
+  if (h->shared_cost) {
+    // Column of C of each plan column: its index in the measure's unpruned
+    // support.  keep[] counts from the start of the descriptions, so the
+    // measure's unpruned start there is subtracted.
+    std::vector<int> cc(h->T);
+    {
+      long long start = 0;  // unpruned offset of measure m in the description
+      int mi = 0;
+      for (int i = 0; i < n; ++i) {
+        const mam_desc& d = descs[i];
+        for (int m = 0; m < d.M; ++m) {
+          if (!(m < mb || m >= me)) {
+            for (long long c = h->col_off[mi]; c < h->col_off[mi + 1]; ++c)
+              cc[c] = int(h->keep[c] - start);
+            ++mi;
+          }
+          start += d.S[m];
+        }
+      }
+    }
+    if ((s = upload(h, h->cost_col, cc.data(), cc.size())) != MAM_OK) return bail(s);
+    std::vector<int> zeros(h->n_sup, 0);
+    const double one = 1.0, eta0 = d0.eta;
+    if ((s = upload(h, h->sup_meas_d, zeros.data(), zeros.size())) != MAM_OK) return bail(s);
+    if ((s = upload(h, h->sup_alpha_d, &one, 1)) != MAM_OK) return bail(s);
+    if ((s = upload(h, h->sup_eta_d, &eta0, 1)) != MAM_OK) return bail(s);
+    if ((s = upload(h, h->sup_zeta_d, d0.zeta, size_t(h->n_sup) * h->dim)) != MAM_OK)
+      return bail(s);
   }
   if ((s = upload(h, h->q, q32.data(), q32.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->q64, q64.data(), q64.size())) != MAM_OK) return bail(s);
@@ -888,9 +1100,15 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out) {
         }
         e = cudaMemcpy(zeta_d, zk.data(), sizeof(double) * zk.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { s = cuda_fail(h, e, "zeta upload"); break; }
-        e = launch_build_cost(h->cost_dtype, h->cost, xi_d, zeta_d, nullptr,
-                              h->col_meas, h->alpha_d, h->eta_d, c0, c1 - c0, h->R, h->ld,
-                              h->dim, h->stream);
+        if (h->shared_cost)  // one matrix C over the common support (xi is shared too)
+          e = i == 0 ? launch_build_cost(h->cost_dtype, h->cost, xi_d, h->sup_zeta_d, nullptr,
+                                         h->sup_meas_d, h->sup_alpha_d, h->sup_eta_d, 0,
+                                         h->n_sup, h->R, h->ld, h->dim, h->stream)
+                     : cudaSuccess;
+        else
+          e = launch_build_cost(h->cost_dtype, h->cost, xi_d, zeta_d, nullptr,
+                                h->col_meas, h->alpha_d, h->eta_d, c0, c1 - c0, h->R, h->ld,
+                                h->dim, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { s = cuda_fail(h, e, "cost kernel"); break; }
       } else {
@@ -945,6 +1163,12 @@ mam_status mam_create(const mam_desc* desc, mam_problem** out) {
   return create_impl(1, desc, out);
 }
 
+mam_status mam_create_sharded(const mam_desc* desc, const mam_shard* shard,
+                              mam_problem** out) {
+  if (!shard) return fail(nullptr, MAM_ERR_INVALID_ARG, "shard is NULL");
+  return create_impl(1, desc, out, shard);
+}
+
 mam_status mam_batch_create(int32_t n, const mam_desc* descs, mam_problem** out) {
   return create_impl(n, descs, out);
 }
@@ -967,11 +1191,20 @@ static mam_status objective_all(mam_problem* h, std::vector<mam_objective_t>& ou
                               h->sched_d, draw_args(h), h->iter_d, h->P, h->diag_out,
                               h->stream),
            "diagnostic reduction");
-  const int nblk = avg_blocks(h);
+  // Sharded: the rank's column sums and block sums, summed over the ranks
+  // (the block sums of the last averaging are the rank's own, so this is the
+  // same global value whether or not the last iteration exchanged them).
+  if (h->sharded) {
+    MAM_TRY(shard_exchange(h, h->diag_out, 3, MAM_SUM_F64));
+    MAM_TRY(shard_block_sums(h));
+    MAM_TRY(shard_exchange(h, h->passes, 1, MAM_SUM_I64));
+  }
+  const int nblk = h->sharded ? 1 : avg_blocks(h);
   std::vector<double> sums(size_t(h->P) * 3), blk(size_t(h->P) * nblk * 4), t(h->P);
   unsigned long long passes = 0;
   MAM_CUDA(cudaMemcpyAsync(sums.data(), h->diag_out, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream), "read");
-  MAM_CUDA(cudaMemcpyAsync(blk.data(), h->blk, sizeof(double) * blk.size(), cudaMemcpyDeviceToHost, h->stream), "read");
+  MAM_CUDA(cudaMemcpyAsync(blk.data(), h->sharded ? h->blk_glob : h->blk,
+                           sizeof(double) * blk.size(), cudaMemcpyDeviceToHost, h->stream), "read");
   MAM_CUDA(cudaMemcpyAsync(&passes, h->passes, sizeof(passes), cudaMemcpyDeviceToHost, h->stream), "read");
   MAM_CUDA(cudaMemcpyAsync(t.data(), h->t_used, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, h->stream), "read");
   MAM_TRY(sync(h));
@@ -1064,6 +1297,8 @@ mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol, double w
 mam_status mam_update_support(mam_problem* h, double* xi_out) {
   MAM_CHECK_HANDLE(h);
   if (h->P != 1) return fail(h, MAM_ERR_INVALID_ARG, "the support step needs a single problem");
+  if (h->sharded)
+    return fail(h, MAM_ERR_INVALID_ARG, "the support step is not offered for sharded problems");
   if (h->nb > 1)
     return fail(h, MAM_ERR_INVALID_ARG, "the support step needs the deterministic index set");
   if (h->has_gen_cost || h->zeta_kept.size() != size_t(h->T) * h->dim)
@@ -1113,6 +1348,7 @@ mam_status mam_update_support(mam_problem* h, double* xi_out) {
   a.col_meas = h->col_meas;
   a.delta32 = h->delta32;
   a.inv_rho = h->irho_m;
+  a.cost_col = h->cost_col;
   a.alpha = h->alpha_d;
   a.zeta = h->zeta_dev;
   a.acc = h->sup_acc;
@@ -1128,9 +1364,13 @@ mam_status mam_update_support(mam_problem* h, double* xi_out) {
   a.dim = h->dim;
   MAM_CUDA(launch_support_step(h->cost_dtype, a, h->xi_dev, h->stream), "support step");
   // The costs of the new support (FP64, rounded to the storage type).
-  MAM_CUDA(launch_build_cost(h->cost_dtype, h->cost, h->xi_dev, h->zeta_dev, nullptr,
-                             h->col_meas, h->alpha_d, h->eta_d, 0, h->T, h->R, h->ld, h->dim,
-                             h->stream),
+  MAM_CUDA(h->shared_cost
+               ? launch_build_cost(h->cost_dtype, h->cost, h->xi_dev, h->sup_zeta_d, nullptr,
+                                   h->sup_meas_d, h->sup_alpha_d, h->sup_eta_d, 0, h->n_sup,
+                                   h->R, h->ld, h->dim, h->stream)
+               : launch_build_cost(h->cost_dtype, h->cost, h->xi_dev, h->zeta_dev, nullptr,
+                                   h->col_meas, h->alpha_d, h->eta_d, 0, h->T, h->R, h->ld,
+                                   h->dim, h->stream),
            "cost kernel");
   MAM_CUDA(cudaMemcpyAsync(h->xi_h.data(), h->xi_dev, sizeof(double) * h->xi_h.size(),
                            cudaMemcpyDeviceToHost, h->stream),
@@ -1145,6 +1385,8 @@ mam_status mam_free_support(mam_problem* h, int32_t outer, int32_t inner_iters, 
   MAM_CHECK_HANDLE(h);
   if (outer < 0 || inner_iters < 0 || check_every < 1 || !(gap_tol >= 0))
     return fail(h, MAM_ERR_INVALID_ARG, "bad free-support arguments");
+  if (h->sharded)
+    return fail(h, MAM_ERR_INVALID_ARG, "the support step is not offered for sharded problems");
   int total = 0;
   for (int k = 0; k < outer; ++k) {
     // Algorithm 2: the fixed-support problem on the current support ...
@@ -1202,6 +1444,26 @@ mam_status mam_get_theta(mam_problem* h, float* theta_out) {
                              cudaMemcpyDeviceToHost, h->stream),
            "theta copy");
   return sync(h);
+}
+
+mam_status mam_get_theta_range(mam_problem* h, int64_t col0, int64_t ncols, float* theta_out) {
+  MAM_CHECK_HANDLE(h);
+  if (!theta_out) return fail(h, MAM_ERR_INVALID_ARG, "theta_out is NULL");
+  if (col0 < 0 || ncols < 0 || col0 + ncols > h->T)
+    return fail(h, MAM_ERR_INVALID_ARG, "column range outside 0..T");
+  if (ncols == 0) return MAM_OK;
+  MAM_CUDA(cudaMemcpy2DAsync(theta_out, sizeof(float) * h->R, h->theta + size_t(col0) * h->ld,
+                             sizeof(float) * h->ld, sizeof(float) * h->R, size_t(ncols),
+                             cudaMemcpyDeviceToHost, h->stream),
+           "theta copy");
+  return sync(h);
+}
+
+mam_status mam_get_work(const mam_problem* h, int64_t* columns, int64_t* entries) {
+  if (!h) return fail(nullptr, MAM_ERR_INVALID_ARG, "null handle");
+  if (columns) *columns = h->work_cols;
+  if (entries) *entries = h->work_entries;
+  return MAM_OK;
 }
 
 mam_status mam_get_sizes(const mam_problem* h, int32_t* n_problems, int32_t* n_measures,

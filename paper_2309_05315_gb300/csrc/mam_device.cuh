@@ -222,6 +222,14 @@ __device__ __forceinline__ float i64_to_f32(long long v) {
   return fmaf(float(hi), 4294967296.f, float(lo));
 }
 
+// floor(x * a / 2^62) for |x| < 2^63, 0 <= a <= 2^62 (exact): the product of
+// a fixed-point marginal and an averaging weight a_m held as round(a_m 2^62).
+__device__ __forceinline__ long long mul_q62(long long x, long long a) {
+  const long long hi = __mul64hi(x, a);
+  const unsigned long long lo = (unsigned long long)x * (unsigned long long)a;
+  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -230,8 +238,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Index set of column step k (Remark 2): bundle i is drawn with probability
 // beta_i from u_k = (SplitMix64(seed + (k+1) * 0x9E3779B97F4A7C15) >> 11)
-// * 2^-53.  Deterministic MAM (nb <= 1) always uses index set 0.
-__device__ __forceinline__ int draw_index_set(const Draw& d, long long k) {
+// * 2^-53.  Deterministic MAM (nb <= 1) always uses index set 0.  Also called
+// on the host (with a host copy of the cumulative probabilities) to count
+// the work of each step.
+__host__ __device__ __forceinline__ int draw_index_set(const Draw& d, long long k) {
   if (d.nb <= 1) return 0;
   unsigned long long z = d.seed + (unsigned long long)k * 0x9E3779B97F4A7C15ull;
   z += 0x9E3779B97F4A7C15ull;

@@ -11,8 +11,10 @@
 
 namespace mam {
 
-constexpr int kGraphIters = 10;  // iterations per captured CUDA graph
-constexpr int kMaxR = 12288;     // largest column a CTA covers (threads*vec*4)
+constexpr int kGraphIters = 10;   // iterations per captured CUDA graph
+constexpr int kMaxCtaR = 12288;   // largest column one CTA covers (threads*vec*4)
+constexpr int kMaxR = 786432;     // largest column a cluster of 16 CTAs covers
+                                  // (49152 rows of w, 192 KB, per CTA)
 
 struct BackwardState;  // mam_backward.cu
 
@@ -111,15 +113,52 @@ struct mam_problem {
   // host mirrors
   long long iter = 0;
   long long diag_iter = -1;
+  // work done by the column steps since create (mam_get_work)
+  long long work_cols = 0;
+  long long work_entries = 0;
 
   // per-kernel timing (mam_profile_enable)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
 
+  // shared cost layout (MAM_COST_SHARED): one matrix C over the common support
+  bool shared_cost = false;
+  int n_sup = 0;                  // columns of C (points of the common support)
+  int* cost_col = nullptr;        // [T] column of C of each plan column
+  float* cmul = nullptr;          // [Mtot] alpha_m (shared) or 1: factor of the stored cost
+  double* sup_zeta_d = nullptr;   // [n_sup][dim] the common support points
+  int* sup_meas_d = nullptr;      // [n_sup] zeros (C is built as one unit-weight measure)
+  double* sup_alpha_d = nullptr;  // [1] 1.0
+  double* sup_eta_d = nullptr;    // [1] eta
+
+  // measure-sharded problem (mam_create_sharded): measures m_begin ..
+  // m_begin + Mtot - 1 of M_global live here
+  bool sharded = false;
+  int m_begin = 0, M_global = 0;
+  mam_allreduce_fn allreduce = nullptr;
+  void* ar_user = nullptr;
+  long long* exch_i64 = nullptr;  // [R] partial, then global, sum of a_m p^(m) F
+  double* exch_f64 = nullptr;     // [R] same for the pi-hat marginals (diagnostics)
+  double* blk_glob = nullptr;     // [4] global sums: D^2, D-hat^2, |dp|^2, 0
+
   mam::BackwardState* bwd = nullptr;
   unsigned* amask = nullptr;  // set during the reverse sweep's recomputation only
 };
+
+// Early returns on a failed library call (MAM_TRY) or CUDA call (MAM_CUDA;
+// needs the handle `h` in scope).
+#define MAM_TRY(x)                     \
+  do {                                 \
+    mam_status _s = (x);               \
+    if (_s != MAM_OK) return _s;       \
+  } while (0)
+
+#define MAM_CUDA(x, where)                                 \
+  do {                                                     \
+    cudaError_t _e = (x);                                  \
+    if (_e != cudaSuccess) return mam::cuda_fail(h, _e, where); \
+  } while (0)
 
 namespace mam {
 
@@ -164,5 +203,11 @@ struct Piece {
 };
 std::vector<Piece> state_pieces(mam_problem* h);
 mam_status reset_state(mam_problem* h);
+
+// Measure-sharded problems (mam_shard.cu).
+int shard_blocks(const mam_problem* h);
+mam_status shard_exchange(mam_problem* h, void* buf, long long count, int dtype);
+mam_status shard_block_sums(mam_problem* h);
+mam_status shard_average(mam_problem* h, int reduce, bool diag);
 
 }  // namespace mam

@@ -31,7 +31,9 @@ struct Draw {
 // accumulation of row sums, t^k, and the fused diagnostics).
 struct ColArgs {
   float* theta;              // [T][ld] plans, column-contiguous
-  const void* cost;          // [T][ld] costs (float / bf16 / half)
+  const void* cost;          // [T][ld] costs (float / bf16 / half), or [S][ld] shared
+  const int* cost_col;       // [T] cost column of each plan column (shared layout), or null
+  const float* cmul;         // [Mtot] factor of the stored cost: alpha_m (shared), else 1
   const float* q;            // [T] kept weights q_s (the simplex masses)
   float* lam;                // [T] last threshold lambda_s (NaN: none)
   float* nact;               // [T] active-set size at that threshold (0: none)
@@ -124,6 +126,15 @@ cudaError_t launch_column_ring(int nv, int cost_dtype, bool diag, int grid, int 
 cudaError_t set_column_ring_smem(int nv, int cost_dtype, bool diag, size_t smem);
 cudaError_t column_ring_occupancy(int nv, int cost_dtype, bool diag, int threads,
                                   size_t smem, int* blocks_per_sm);
+// One column per thread-block cluster of cs CTAs (mam_cluster_kernel.cu),
+// for columns longer than one CTA holds.
+int cluster_rows_per_cta(int ld, int cs);
+size_t cluster_kernel_smem(int ld, int cs);
+cudaError_t launch_column_cluster(int cost_dtype, bool diag, int cs, int grid, int threads,
+                                  size_t smem, cudaStream_t st, const ColArgs& a);
+cudaError_t set_column_cluster_smem(int cost_dtype, bool diag, size_t smem);
+cudaError_t column_cluster_occupancy(int cost_dtype, bool diag, int cs, int threads,
+                                     size_t smem, int* clusters);
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const double* zeta, const double* gen_cost,
                               const int* col_meas, const double* alpha,
@@ -141,7 +152,8 @@ cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                const long long* iter, int P, double* out,
                                cudaStream_t st);
 
-cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
+cudaError_t launch_lb(int cost_dtype, const void* cost, const int* cost_col,
+                      const float* cmul, const float* q,
                       const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,

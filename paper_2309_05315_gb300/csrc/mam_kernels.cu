@@ -112,8 +112,9 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
       mbar_expect_tx(&bar[s], bytes_th + bytes_c);
       bulk_load(th_s + size_t(s) * tile, A.theta + size_t(col) * ld, bytes_th,
                 &bar[s]);
+      const long long ccol = A.cost_col ? (long long)A.cost_col[col] : col;
       bulk_load(c_s + size_t(s) * tile,
-                static_cast<const CT*>(A.cost) + size_t(col) * ld, bytes_c,
+                static_cast<const CT*>(A.cost) + size_t(ccol) * ld, bytes_c,
                 &bar[s]);
     };
     if (tid == 0) {
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
       }
     };
 
-    float rho_m = 0.f;
+    float rho_m = 0.f, cm = 1.f;  // cm: factor of the stored cost (diagnostics)
     f2_t nirho2 = 0ull;
     const f2_t two2 = pk(2.f, 2.f);
     int m_cur = -1, p_cur = -1;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
           if (tid == 0) A.t_used[pr] = t_cur;
         }
         rho_m = A.rho[m];
+        if (DIAG) cm = A.cmul[m];
         nirho2 = pk(-A.inv_rho[m], -A.inv_rho[m]);
         acc_m = A.acc + size_t(m) * R;
         const float* dl = A.delta32 + size_t(m) * ld;
@@ -215,8 +217,8 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
         fa = add2(fa, relu2(x0, n));
         fb = add2(fb, relu2(x1, n));
         if (DIAG) {
-          lbmin = fminf(lbmin, fminf(fminf(c.x - rho_m * dd.x, c.y - rho_m * dd.y),
-                                     fminf(c.z - rho_m * dd.z, c.w - rho_m * dd.w)));
+          lbmin = fminf(lbmin, fminf(fminf(cm * c.x - rho_m * dd.x, cm * c.y - rho_m * dd.y),
+                                     fminf(cm * c.z - rho_m * dd.z, cm * c.w - rho_m * dd.w)));
         }
       }
       // The failure flag rides in the first reduction (f < 0 marks it).
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
             const float4 th = reinterpret_cast<const float4*>(ths)[idx];
             const float4 c = CostIO<CT>::load4(cs, idx);
             const float thv[4] = {th.x, th.y, th.z, th.w};
-            const float cv[4] = {c.x, c.y, c.z, c.w};
+            const float cv[4] = {cm * c.x, cm * c.y, cm * c.z, cm * c.w};
             const float ovv[4] = {ov.x, ov.y, ov.z, ov.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -417,13 +419,6 @@ __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
 // row, threadIdx.y a slice of the measures (m = m0 + y + k SL), so each
 // thread walks several measures with independent loads; slices are combined
 // in shared memory.  Grid (ceil(R / rows), P).
-__device__ __forceinline__ long long mul_q62(long long x, long long a) {
-  // floor(x * a / 2^62) for |x| < 2^63, 0 <= a <= 2^62 (exact)
-  const long long hi = __mul64hi(x, a);
-  const unsigned long long lo = (unsigned long long)x * (unsigned long long)a;
-  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
-}
-
 template <int SL, bool DIAG>
 __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
   constexpr int RX = kAvgThreads / SL;
@@ -722,7 +717,8 @@ __global__ void __launch_bounds__(256) diag_reduce_kernel(
 // One warp per column.
 template <typename CT>
 __global__ void __launch_bounds__(256) lb_kernel(
-    const CT* cost, const float* q, const float* delta32, const double* t_used,
+    const CT* cost, const int* cost_col, const float* cmul, const float* q,
+    const float* delta32, const double* t_used,
     const int* meas_prob, const float* rho, const int* col_meas, long long T,
     int R, int ld, float lb_cap, float* diag_lb) {
   const int lane = threadIdx.x & 31;
@@ -733,14 +729,15 @@ __global__ void __launch_bounds__(256) lb_kernel(
     const float tt = float(t_used[meas_prob[m]]);
     const float rh = rho[m];
     const float* dl = delta32 + size_t(m) * ld;
-    const CT* cc = cost + size_t(col) * ld;
+    const CT* cc = cost + size_t(cost_col ? (long long)cost_col[col] : col) * ld;
+    const float cm = cmul[m];
     float mn = INFINITY;
     for (int r = lane; r < R; r += 32) {
       float c;
       if constexpr (sizeof(CT) == 4) c = float(cc[r]);
       else if constexpr (std::is_same<CT, __half>::value) c = __half2float(cc[r]);
       else c = __bfloat162float(cc[r]);
-      mn = fminf(mn, c - rh * __fmul_rn(tt, dl[r]));
+      mn = fminf(mn, cm * c - rh * __fmul_rn(tt, dl[r]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -749,22 +746,13 @@ __global__ void __launch_bounds__(256) lb_kernel(
 }
 
 template <int NV, typename CT, bool DIAG>
-cudaError_t launch_col_t(int grid, int threads, size_t smem, cudaStream_t st,
-                         const ColArgs& a) {
-  return launch_pdl(column_kernel<NV, CT, DIAG>, dim3(grid), dim3(threads), smem, st, a);
-}
-
-template <int NV, typename CT, bool DIAG>
-cudaError_t smem_col_t(size_t smem) {
-  return cudaFuncSetAttribute(column_kernel<NV, CT, DIAG>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(smem));
-}
-
-template <int NV, typename CT, bool DIAG>
-cudaError_t occ_col_t(int threads, size_t smem, int* n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      n, column_kernel<NV, CT, DIAG>, threads, smem);
+cudaError_t col_op_k(int op, int grid, int threads, size_t smem, cudaStream_t st,
+                     const ColArgs* a, int* occ) {
+  auto kern = column_kernel<NV, CT, DIAG>;
+  if (op == 0) return launch_pdl(kern, dim3(grid), dim3(threads), smem, st, *a);
+  if (op == 1)
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, smem);
 }
 
 // Dispatch over the compile-time (NV, cost type, DIAG) variants.
@@ -773,13 +761,8 @@ cudaError_t occ_col_t(int threads, size_t smem, int* n) {
 template <int NV, typename CT>
 cudaError_t col_op(int op, bool diag, int grid, int threads, size_t smem,
                    cudaStream_t st, const ColArgs* a, int* occ) {
-  if (op == 0)
-    return diag ? launch_col_t<NV, CT, true>(grid, threads, smem, st, *a)
-                : launch_col_t<NV, CT, false>(grid, threads, smem, st, *a);
-  if (op == 1)
-    return diag ? smem_col_t<NV, CT, true>(smem) : smem_col_t<NV, CT, false>(smem);
-  return diag ? occ_col_t<NV, CT, true>(threads, smem, occ)
-              : occ_col_t<NV, CT, false>(threads, smem, occ);
+  return diag ? col_op_k<NV, CT, true>(op, grid, threads, smem, st, a, occ)
+              : col_op_k<NV, CT, false>(op, grid, threads, smem, st, a, occ);
 }
 
 template <typename CT>
@@ -923,7 +906,8 @@ cudaError_t launch_rowsum(const float* theta, const long long* col_off,
   return cudaGetLastError();
 }
 
-cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
+cudaError_t launch_lb(int cost_dtype, const void* cost, const int* cost_col,
+                      const float* cmul, const float* q,
                       const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
@@ -933,13 +917,13 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const float* q,
   if (g < 1) g = 1;
   switch (cost_dtype) {
     case 0:
-      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
+      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), cost_col, cmul, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     case 1:
-      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
+      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), cost_col, cmul, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     case 2:
-      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
+      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), cost_col, cmul, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     default:
       return cudaErrorInvalidValue;

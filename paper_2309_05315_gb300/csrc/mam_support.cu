@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(256) support_accumulate_kernel(const SupportAr
     const int m = A.col_meas[col];
     const float irho = A.inv_rho[m];
     const float* th = A.theta + size_t(col) * A.ld;
-    const CT* cc = static_cast<const CT*>(A.cost) + size_t(col) * A.ld;
+    const CT* cc = static_cast<const CT*>(A.cost) +
+                   size_t(A.cost_col ? (long long)A.cost_col[col] : col) * A.ld;
     const float* dl = A.delta32 + size_t(m) * A.ld;
     auto w_at = [&](int r) {
       return fmaf(-cost_at(cc, r), irho, fmaf(2.f, __fmul_rn(A.t, dl[r]), th[r]));

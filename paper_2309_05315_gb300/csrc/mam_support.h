@@ -8,7 +8,8 @@ namespace mam {
 // Arguments of the free-support step (Algorithm 2, Prop. 4).
 struct SupportArgs {
   const float* theta;        // [T][ld]
-  const void* cost;          // [T][ld] (float / bf16 / half)
+  const void* cost;          // [T][ld] (float / bf16 / half), or [S][ld] shared
+  const int* cost_col;       // [T] cost column of each plan column (shared), or null
   const float* q;            // [T]
   const float* lam;          // [T] last thresholds (warm start; NaN: none)
   const int* col_meas;       // [T]

@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
       const long long col = c0 + j;
       mbar_expect_tx(&full[s], bytes_th + bytes_c);
       bulk_load(th_s + size_t(s) * kSlot, A.theta + size_t(col) * ld, bytes_th, &full[s]);
-      bulk_load(c_s + size_t(s) * kSlot, static_cast<const CT*>(A.cost) + size_t(col) * ld,
+      const long long ccol = A.cost_col ? (long long)A.cost_col[col] : col;
+      bulk_load(c_s + size_t(s) * kSlot, static_cast<const CT*>(A.cost) + size_t(ccol) * ld,
                 bytes_c, &full[s]);
       __threadfence_block();  // the arrive and the copies precede the count
       atomicAdd(&issued_cnt[s], 1);
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
     int p_cur = -1;
     float tf = 1.f;
     int m_cur = -1;
-    float irho = 0.f, rho_m = 0.f;
+    float irho = 0.f, rho_m = 0.f, cm = 1.f;  // cm: factor of the stored cost (diagnostics)
     while (true) {
       int jj = 0;
       if (lane == 0) jj = atomicAdd(next, 1);
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
         }
         irho = A.inv_rho[m];
         rho_m = A.rho[m];
+        if (DIAG) cm = A.cmul[m];
       }
       const float* dm = A.delta32 + size_t(m) * ld;
       const float* ths = th_s + size_t(s) * kSlot;
@@ -291,8 +293,9 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
         w[v][2] = fmaf(-c.z, irho, fmaf(2.f, d.z, th.z));
         w[v][3] = fmaf(-c.w, irho, fmaf(2.f, d.w, th.w));
         if (DIAG)
-          lbmin = fminf(fminf(fminf(lbmin, c.x - rho_m * d.x), fminf(c.y - rho_m * d.y, c.z - rho_m * d.z)),
-                        c.w - rho_m * d.w);
+          lbmin = fminf(fminf(fminf(lbmin, cm * c.x - rho_m * d.x),
+                              fminf(cm * c.y - rho_m * d.y, cm * c.z - rho_m * d.z)),
+                        cm * c.w - rho_m * d.w);
       }
       if (!DIAG) {
         __syncwarp();  // every lane has read the slot
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(RingMaxThreads<NV>::value)
           if (DIAG) {
             const float4 c = CostIO<CT>::load4(cs, g);
             const float4 th = reinterpret_cast<const float4*>(ths)[g];
-            const float cv[4] = {c.x, c.y, c.z, c.w};
+            const float cv[4] = {cm * c.x, cm * c.y, cm * c.z, cm * c.w};
             const float ov[4] = {o.x, o.y, o.z, o.w};
             const float tv[4] = {th.x, th.y, th.z, th.w};
 #pragma unroll

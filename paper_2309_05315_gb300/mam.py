@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _capi
-from ._capi import MamDesc, MamKernelConfig, MamObjective, check
+from ._capi import MamDesc, MamKernelConfig, MamObjective, MamShard, check
 
 
 def _dptr(a: np.ndarray):
@@ -26,7 +26,7 @@ class _DescKeep:
     """Owns the contiguous arrays a mam_desc points into."""
 
     def __init__(self, problem, cost_dtype, theta0_mode, diag_mode, n_bundles,
-                 seed, rho, gamma, stream, capped=False, eta=0.0):
+                 seed, rho, gamma, stream, capped=False, eta=0.0, cost_layout="per_column"):
         M = len(problem.q)
         xi = np.ascontiguousarray(problem.xi, dtype=np.float64)
         if xi.ndim == 1:
@@ -66,6 +66,7 @@ class _DescKeep:
         d.stream = stream
         d.eta = float(eta)
         d.capped = 1 if capped else 0
+        d.cost_layout = _capi.COST_LAYOUTS[cost_layout]
         self.desc = d
 
 
@@ -81,19 +82,35 @@ class Mam:
                  diag: str = "last", n_bundles: Optional[int] = None,
                  seed: int = 0, rho: Optional[float] = None,
                  gamma: Optional[float] = None, stream=None,
-                 capped: bool = False, eta: float = 0.0):
+                 capped: bool = False, eta: float = 0.0, shard=None,
+                 cost_layout: str = "per_column"):
+        """``cost_layout="shared"`` stores one cost matrix for measures on a
+        common support (mam_desc.cost_layout).
+        ``shard=(m_begin, m_end, allreduce)`` creates this rank's part of a
+        measure-sharded problem (mam_create_sharded); ``allreduce`` is a
+        ctypes ``_capi.ALLREDUCE_FN`` (see ``paper_2309_05315_gb300.shard``),
+        kept alive with the handle."""
         L = _capi.lib()
         if (problem is None) == (problems is None):
             raise ValueError("give exactly one of problem / problems")
+        if shard is not None and problems is not None:
+            raise ValueError("a sharded problem is a single problem")
         probs = [problem] if problems is None else list(problems)
         st = None
         if stream is not None:
             st = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         keeps = [_DescKeep(p, cost_dtype, theta0, diag, n_bundles, seed, rho, gamma, st,
-                           capped, eta)
+                           capped, eta, cost_layout)
                  for p in probs]
         self._h = C.c_void_p()
-        if problems is None:
+        self._shard = None
+        if shard is not None:
+            m0, m1, fn = shard
+            self._shard_fn = fn   # the callback must outlive the handle
+            self._shard = MamShard(int(m0), int(m1), fn, None)
+            check(L.mam_create_sharded(C.byref(keeps[0].desc), C.byref(self._shard),
+                                       C.byref(self._h)))
+        elif problems is None:
             check(L.mam_create(C.byref(keeps[0].desc), C.byref(self._h)))
         else:
             arr = (MamDesc * len(keeps))(*[k.desc for k in keeps])
@@ -194,6 +211,20 @@ class Mam:
         out = np.empty((self.T, self.R), dtype=np.float32)
         self._check(_capi.lib().mam_get_theta(self._h, out.ctypes.data))
         return out
+
+    def theta_columns(self, col0: int, ncols: int) -> np.ndarray:
+        """Columns col0 .. col0 + ncols - 1 of the plans, [ncols][R] FP32."""
+        out = np.empty((int(ncols), self.R), dtype=np.float32)
+        self._check(_capi.lib().mam_get_theta_range(self._h, int(col0), int(ncols),
+                                                    out.ctypes.data))
+        return out
+
+    def work(self) -> dict:
+        """Columns projected and plan entries updated by the column steps so
+        far (the index sets actually drawn)."""
+        c, e = C.c_int64(), C.c_int64()
+        self._check(_capi.lib().mam_get_work(self._h, C.byref(c), C.byref(e)))
+        return {"columns": c.value, "entries": e.value}
 
     def pruned_sizes(self) -> np.ndarray:
         out = np.empty(self.n_measures, dtype=np.int32)

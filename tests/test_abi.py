@@ -124,3 +124,27 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_capi, "_lib", None)
     with pytest.raises(ImportError):
         _capi.lib()
+
+
+def test_shared_cost_layout_needs_one_support(L):
+    """MAM_COST_SHARED: every measure must have the same support points, and
+    the cost must be the squared Euclidean one; checked before any device
+    call."""
+    d, keep = make_desc(S=(3, 3), cost_layout=1)
+    zeta = np.zeros((6, 2))
+    zeta[4, 1] = 0.5                                  # measure 1 differs in one point
+    keep["zeta"] = zeta
+    d.zeta = zeta.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    assert L.mam_create(C.byref(d), C.byref(h)) == 1
+    assert b"same support" in L.mam_last_error(None)
+    d2, keep2 = make_desc(S=(3, 2), cost_layout=1, q=[1 / 3] * 3 + [0.5, 0.5])
+    assert L.mam_create(C.byref(d2), C.byref(h)) == 1
+    cost = np.ones((5, 4))
+    d3, keep3 = make_desc(S=(3, 2), q=[1 / 3] * 3 + [0.5, 0.5], cost_layout=1)
+    d3.cost = cost.ctypes.data_as(C.POINTER(C.c_double))
+    assert L.mam_create(C.byref(d3), C.byref(h)) == 1
+    assert b"cost = NULL" in L.mam_last_error(None)
+    d4, keep4 = make_desc(cost_layout=2)
+    assert L.mam_create(C.byref(d4), C.byref(h)) == 1
+    assert b"cost_layout" in L.mam_last_error(None)

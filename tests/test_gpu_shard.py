@@ -1,0 +1,221 @@
+"""GPU parity of the measure-sharded solver (mam_create_sharded).
+
+The ranks run on the one GPU as host threads, each with its own handle and
+stream.  Their exchange copies each rank's buffer to the host, meets at a
+barrier, and writes the rank-ordered sum back (no kernel ever waits for
+another rank: the host does).  Checked against the unsharded solver:
+* balanced problems: the barycenter p and every plan bit for bit, for 20
+  iterations, with 2 and 3 ranks, deterministic and randomized index sets
+  (p is an exact integer sum whichever rank holds a measure);
+* gamma finite: t^k takes its distance from an FP64 sum whose association
+  depends on the partition, so the iterates agree to rounding, and both
+  follow the FP64 oracle (Algorithm 1) to 1e-5;
+* diagnostics (summed over the ranks) agree with the unsharded ones;
+* the operations a sharded handle does not offer are refused, and a failing
+  exchange gives MAM_ERR_COMM.
+"""
+import math
+import threading
+
+import numpy as np
+import pytest
+
+from oracle.mam_oracle import MamOracle, prepare
+from workloads import config1, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+ITER_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def Mam():
+    from paper_2309_05315_gb300.build import build
+    build()
+    from paper_2309_05315_gb300 import Mam as _Mam
+    return _Mam
+
+
+class HostExchange:
+    """Sums a buffer over the ranks through host memory."""
+
+    def __init__(self, n, fail_rank=None):
+        self.n = n
+        self.bar = threading.Barrier(n, timeout=120)
+        self.slots = [None] * n
+        self.fail_rank = fail_rank
+        self.calls = 0
+
+    def callback(self, rank):
+        import torch
+        from paper_2309_05315_gb300 import _capi
+        from paper_2309_05315_gb300.shard import buffer_view
+
+        def cb(buf, count, dtype, stream, user):
+            try:
+                if rank == self.fail_rank and self.calls > 4:
+                    self.bar.abort()
+                    return 7
+                t = buffer_view(buf, count, dtype)
+                s = torch.cuda.ExternalStream(int(stream or 0))
+                with torch.cuda.stream(s):
+                    self.slots[rank] = t.cpu()
+                self.bar.wait()
+                total = self.slots[0].clone()
+                for r in range(1, self.n):
+                    total += self.slots[r]
+                self.bar.wait()
+                with torch.cuda.stream(s):
+                    t.copy_(total.to(t.device, non_blocking=False))
+                s.synchronize()
+                if rank == 0:
+                    self.calls += 1
+                return 0
+            except threading.BrokenBarrierError:
+                return 9
+
+        return _capi.ALLREDUCE_FN(cb)
+
+
+def run_ranks(Mam, prob, n, iters, per_step=None, ranges=None, fail_rank=None, **kw):
+    """Create n sharded handles in threads, step them `iters` times (calling
+    per_step(rank, handle, k) after each step); returns per-rank results."""
+    from paper_2309_05315_gb300.shard import partition_measures
+    if ranges is None:
+        S = [int((np.asarray(q) > 0).sum()) for q in prob.q]
+        ranges = partition_measures(S, n)
+    ex = HostExchange(n, fail_rank)
+    fns = [ex.callback(r) for r in range(n)]
+    out = [None] * n
+    errs = [None] * n
+
+    def body(rank):
+        try:
+            with Mam(prob, shard=(*ranges[rank], fns[rank]), **kw) as h:
+                res = {"traj": []}
+                for k in range(iters):
+                    h.step(1)
+                    if per_step:
+                        res["traj"].append(per_step(rank, h, k))
+                res["theta"] = h.theta()
+                res["p"] = h.barycenter()
+                res["obj"] = h.objective() if kw.get("diag") == "last" else None
+                out[rank] = res
+        except Exception as e:   # noqa: BLE001 - reported to the test
+            errs[rank] = e
+            ex.bar.abort()
+
+    th = [threading.Thread(target=body, args=(r,)) for r in range(n)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=600)
+    return out, errs, ranges
+
+
+def unsharded(Mam, prob, iters, **kw):
+    traj = []
+    with Mam(prob, **kw) as h:
+        for _ in range(iters):
+            h.step(1)
+            traj.append(h.barycenter().copy())
+        th = h.theta()
+        obj = h.objective() if kw.get("diag") == "last" else None
+        S = h.pruned_sizes()
+    return traj, th, obj, S
+
+
+@pytest.mark.parametrize("n, kw", [
+    (2, dict()),
+    (3, dict()),
+    (2, dict(n_bundles=3, seed=9)),
+])
+def test_sharded_balanced_is_bitwise_unsharded(Mam, n, kw):
+    prob = tiny_problem(500, M=6, K=8, rho=6.0)
+    iters = 20
+    ref_traj, ref_th, _, S = unsharded(Mam, prob, iters, diag="never", **kw)
+    out, errs, ranges = run_ranks(Mam, prob, n, iters,
+                                  per_step=lambda r, h, k: h.barycenter().copy(),
+                                  diag="never", **kw)
+    assert errs == [None] * n, errs
+    offs = np.concatenate([[0], np.cumsum(S)])
+    for rank in range(n):
+        for k in range(iters):
+            assert np.array_equal(out[rank]["traj"][k], ref_traj[k]), (rank, k)
+        m0, m1 = ranges[rank]
+        assert np.array_equal(out[rank]["theta"], ref_th[offs[m0]:offs[m1]]), rank
+
+
+def test_sharded_config1_default_kernels(Mam):
+    """The blob workload (R = 256) over 3 ranks, one measure each."""
+    prob = config1()
+    iters = 30
+    ref_traj, ref_th, _, S = unsharded(Mam, prob, iters, diag="never")
+    out, errs, ranges = run_ranks(Mam, prob, 3, iters, diag="never")
+    assert errs == [None] * 3, errs
+    offs = np.concatenate([[0], np.cumsum(S)])
+    for rank in range(3):
+        assert np.array_equal(out[rank]["p"], ref_traj[-1])
+        m0, m1 = ranges[rank]
+        assert np.array_equal(out[rank]["theta"], ref_th[offs[m0]:offs[m1]])
+
+
+def test_sharded_unbalanced_follows_oracle_and_unsharded(Mam):
+    gamma = 0.02
+    prob = tiny_problem(501, M=5, K=7, rho=10.0, masses=[0.6, 1.0, 1.4, 0.8, 1.2])
+    iters = 40
+    ref_traj, ref_th, ref_obj, S = unsharded(Mam, prob, iters, diag="last", gamma=gamma)
+    out, errs, ranges = run_ranks(Mam, prob, 2, iters,
+                                  per_step=lambda r, h, k: h.barycenter().copy(),
+                                  diag="last", gamma=gamma)
+    assert errs == [None, None], errs
+    prep = prepare(prob)
+    orc = MamOracle(prep, prob.rho, gamma=gamma)
+    Qa = sum(prep.a[m] * float(prep.q[m].sum()) for m in range(prep.M))
+    for k in range(iters):
+        orc.step(diagnostics=False)
+        for rank in range(2):
+            p = out[rank]["traj"][k]
+            assert np.abs(p - orc.barycenter()).sum() / Qa <= ITER_TOL, (rank, k)
+            assert np.abs(p - ref_traj[k]).sum() / Qa <= 1e-6, (rank, k)
+    for rank in range(2):
+        o = out[rank]["obj"]
+        for key in ("w_hat", "lower_bound", "f_unbal", "dist_pihat", "t"):
+            assert abs(o[key] - ref_obj[key]) <= 1e-5 * abs(ref_obj[key]) + 1e-12, (rank, key)
+        assert o["t"] < 1.0
+
+
+def test_sharded_diagnostics_balanced(Mam):
+    prob = tiny_problem(502, M=4, K=6, rho=8.0)
+    iters = 25
+    _, _, ref_obj, _ = unsharded(Mam, prob, iters, diag="last")
+    out, errs, _ = run_ranks(Mam, prob, 2, iters, diag="last")
+    assert errs == [None, None], errs
+    for rank in range(2):
+        o = out[rank]["obj"]
+        for key in ("w_hat", "lower_bound", "f_unbal", "dist_pihat", "fp_resid", "dp_norm"):
+            assert abs(o[key] - ref_obj[key]) <= 1e-9 * abs(ref_obj[key]) + 1e-14, (rank, key)
+        # dist_L(theta) is summed in FP32 per thread, in an order that depends
+        # on which rank holds a measure
+        assert abs(o["dist_theta"] - ref_obj["dist_theta"]) <= 1e-6 * ref_obj["dist_theta"]
+        assert o["iter"] == iters and o["t"] == 1.0
+
+
+def test_sharded_refusals_and_failing_exchange(Mam):
+    from paper_2309_05315_gb300 import MamError
+    prob = tiny_problem(503, M=4, K=5, rho=8.0)
+
+    def try_ops(rank, h, k):
+        if k == 0:
+            for op in (lambda: h.forward_record(3, 1), lambda: h.update_support(),
+                       lambda: h.autotune(2)):
+                with pytest.raises(MamError) as e:
+                    op()
+                assert e.value.status == 1
+        return None
+
+    out, errs, _ = run_ranks(Mam, prob, 2, 2, per_step=try_ops, diag="never")
+    assert errs == [None, None], errs
+    out, errs, _ = run_ranks(Mam, prob, 2, 20, fail_rank=1, diag="never")
+    assert all(isinstance(e, MamError) for e in errs), errs
+    assert any(e.status == 8 for e in errs), [e.status for e in errs]

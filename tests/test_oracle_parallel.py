@@ -16,6 +16,16 @@ from oracle.parallel import ParallelMamOracle, measure_groups
 from workloads import tiny_problem
 
 
+def test_reduced_precision_costs_built_in_the_workers():
+    prob = tiny_problem(62, M=4, K=4, rho=5.0)
+    seq = MamOracle(prepare(prob, "bf16"), prob.rho)
+    with ParallelMamOracle(prob, cost_dtype="bf16", workers=2) as par:
+        for _ in range(5):
+            a, b = seq.step(diagnostics=True), par.step(diagnostics=True)
+            assert a["w_hat"] == b["w_hat"] and a["lower_bound"] == b["lower_bound"]
+        assert np.array_equal(seq.barycenter(), par.barycenter())
+
+
 def test_measure_groups_are_contiguous_and_balanced():
     S = [5, 1, 1, 9, 2, 2, 2, 8]
     for n in range(1, 10):
@@ -38,7 +48,7 @@ def test_parallel_oracle_is_bitwise_the_sequential_one(kw):
     eta = kw.pop("eta", 0.0)
     prob = tiny_problem(61, M=5, K=5, rho=7.0, masses=masses)
     seq = MamOracle(prepare(prob, eta=eta), prob.rho, **kw)
-    with ParallelMamOracle(prepare(prob, eta=eta), prob.rho, workers=3, **kw) as par:
+    with ParallelMamOracle(prob, prob.rho, eta=eta, workers=3, **kw) as par:
         assert par.workers == 3
         for k in range(12):
             diag = k % 4 == 3

@@ -15,5 +15,7 @@ from .generators import (  # noqa: F401
     config3,
     config4,
     config5,
+    config2_free_support,
+    free_support_grid,
     CONFIGS,
 )

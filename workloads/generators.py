@@ -251,4 +251,24 @@ def config5(i=0, M=100) -> Problem:
                                n_bundles=4, iters=2000)
 
 
+def free_support_grid(M: int, K: int) -> np.ndarray:
+    """Every point sum_m zeta_(m) / M with zeta_(m) on the K x K pixel grid:
+    the (M (K - 1) + 1)^2 points (i / (M (K - 1)), j / (M (K - 1))), the
+    support that contains a barycenter of M images with equal weights
+    (Theorem 1).  Row-major like ``grid_points``."""
+    n = M * (K - 1) + 1
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    return np.stack([i.ravel() / (n - 1), j.ravel() / (n - 1)], axis=1).astype(np.float64)
+
+
+def config2_free_support(i=0, M=10, rho=100.0) -> Problem:
+    """The nested-ellipse images of ``config2`` (60x60, M = 10) on the
+    free-support grid of their barycenter: R = (10 * 59 + 1)^2 = 349281."""
+    p = config2(i, rho=rho)
+    q = p.q[:M]
+    xi = free_support_grid(len(q), p.K)
+    return Problem(name="cfg2_ellipses60_free_support_grid", xi=xi, zeta=p.zeta[:M], q=q,
+                   alpha=np.full(len(q), 1.0 / len(q)), rho=rho, K=p.K, iters=p.iters)
+
+
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
