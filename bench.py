@@ -373,7 +373,10 @@ def time_to_gap(probs, cost_dtype, tol=1e-4, ref_iters=50000, ref_every=100,
 
 def forward_backward(prob, K=200, ckpt=20):
     """Wall time of mam_forward_record(K, ckpt) + mam_backward for
-    L = ||p^K - target||^2 (host gradients), and of K plain iterations."""
+    L = ||p^K - target||^2 (host gradients), and of K plain iterations.
+    ckpt > 0: checkpoints every ckpt iterations, segments recomputed in the
+    backward sweep; ckpt = 0: the active sets of every step kept from the
+    forward pass (when they fit), nothing recomputed."""
     import torch
     from paper_2309_05315_gb300 import Mam
     g = Mam(prob, cost_dtype="f32", diag="never")
@@ -434,6 +437,7 @@ def forms(args):
     out["differentiation"] = {
         "workload": NAMES[4],
         "forward_backward": forward_backward(mix),
+        "forward_backward_all_masks": forward_backward(mix, ckpt=0),
         "plain_f32_time_to_gap_rho300": time_to_gap([mix], "f32", rho=300.0,
                                                     ref_iters=args.gap_ref_iters,
                                                     max_iters=args.gap_ref_iters)}

@@ -69,7 +69,11 @@ typedef enum {
 typedef enum { MAM_F32 = 0, MAM_BF16 = 1, MAM_F16 = 2 } mam_cost_dtype;
 
 /* How the costs are stored (mam_desc.cost_layout). */
-typedef enum { MAM_COST_PER_COLUMN = 0, MAM_COST_SHARED = 1 } mam_cost_layout;
+typedef enum {
+  MAM_COST_PER_COLUMN = 0,
+  MAM_COST_SHARED = 1,
+  MAM_COST_GENERATED = 2
+} mam_cost_layout;
 
 /* When the fused diagnostics (W-hat, dist_L(pi-hat), lower bound, residuals)
  * are computed. */
@@ -138,7 +142,18 @@ typedef struct {
                            the squared Euclidean cost (cost = NULL); in a
                            batch every problem must have the same support,
                            xi and eta.  The stored C is rounded to cost_dtype
-                           before alpha_m is applied.                        */
+                           before alpha_m is applied.
+                           2 (MAM_COST_GENERATED): no cost is stored; the
+                           column kernel computes ||xi_r - zeta_s||^2 (- eta)
+                           in FP32 from FP32 copies of the points (16 B per
+                           row and per column, read through L2) whenever it
+                           needs c: 8 B of HBM traffic per plan entry (theta
+                           read and write) and no T x R cost buffer, for
+                           problems whose costs would not fit or whose
+                           columns are long.  Uses the one-column-per-cluster
+                           kernel (kind 2) for every R; needs the squared
+                           Euclidean cost (cost = NULL); cost_dtype is
+                           ignored.  Reverse mode is not offered.            */
 } mam_desc;
 
 /* Diagnostics of the most recent diagnostic iteration k (all FP64). */
@@ -282,13 +297,24 @@ mam_status mam_get_pruned_sizes(const mam_problem* h, int32_t* S_out);
 
 /* Checkpoint: the whole iteration state (theta, marginals, thresholds,
  * iteration counter, bundle position).  Call with buf = NULL to get *bytes.
- * Resuming with mam_set_state reproduces an uninterrupted run bit for bit. */
+ * Resuming with mam_set_state reproduces an uninterrupted run bit for bit.
+ * Infrastructure for long runs and for the autotuner: the paper has no
+ * counterpart (its state is the plan theta^k of Algorithm 1).  A sharded
+ * handle saves and restores its own measures; every rank must restore the
+ * same iteration. */
 mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes);
 mam_status mam_set_state(mam_problem* h, const void* buf, size_t bytes);
 
 /* Differentiation through K unrolled iterations (balanced, deterministic,
- * single problem).  mam_forward_record restarts from theta^0, runs K
- * iterations and keeps theta every ckpt_every iterations.  mam_backward
+ * single problem).  mam_forward_record restarts from theta^0 and runs K
+ * iterations.  The reverse step of an iteration needs only its active sets
+ * (one bit per plan entry).  ckpt_every > 0: the state is kept every
+ * ckpt_every iterations and mam_backward recomputes each segment (memory:
+ * K/ckpt_every states and ckpt_every masks).  ckpt_every = 0 (automatic):
+ * the masks of all K steps are kept from the forward pass when they fit in a
+ * quarter of the free device memory, and mam_backward recomputes nothing;
+ * otherwise as with ckpt_every = sqrt(K).  The gradients are the same either
+ * way.  mam_backward
  * takes dL/dp^K [R] and writes dL/dq [sum S] (unpruned order, zeros for
  * pruned columns), dL/dzeta [sum S][dim] and dL/dxi [R][dim]; any output may
  * be NULL.  All host pointers.  Only squared Euclidean costs with

@@ -18,7 +18,7 @@ STATUS = {0: "MAM_OK", 1: "MAM_ERR_INVALID_ARG", 2: "MAM_ERR_CUDA", 3: "MAM_ERR_
           7: "MAM_ERR_UNSUPPORTED", 8: "MAM_ERR_COMM"}
 COST_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 DIAG_MODES = {"last": 0, "never": 1, "every": 2}
-COST_LAYOUTS = {"per_column": 0, "shared": 1}
+COST_LAYOUTS = {"per_column": 0, "shared": 1, "generated": 2}
 
 
 class MamDesc(C.Structure):

@@ -100,8 +100,21 @@ mam_status validate(const mam_desc* d, int idx) {
   if (!std::isfinite(d->eta) || d->eta < 0 || (!d->capped && d->eta != 0))
     return fail(nullptr, MAM_ERR_INVALID_ARG,
                 p + "eta must be finite and >= 0, and 0 unless capped is set");
-  if (d->cost_layout != MAM_COST_PER_COLUMN && d->cost_layout != MAM_COST_SHARED)
+  if (d->cost_layout != MAM_COST_PER_COLUMN && d->cost_layout != MAM_COST_SHARED &&
+      d->cost_layout != MAM_COST_GENERATED)
     return fail(nullptr, MAM_ERR_INVALID_ARG, p + "unknown cost_layout");
+  if (d->cost_layout != MAM_COST_PER_COLUMN) {
+    // alpha_m multiplies the unscaled distance inside the kernels, where the
+    // padding rows carry an infinite distance
+    for (int m = 0; m < d->M; ++m)
+      if (!(d->alpha[m] > 0))
+        return fail(nullptr, MAM_ERR_INVALID_ARG,
+                    p + "the shared and generated cost layouts need alpha_m > 0");
+  }
+  if (d->cost_layout == MAM_COST_GENERATED && (d->cost || !d->zeta))
+    return fail(nullptr, MAM_ERR_INVALID_ARG,
+                p + "the generated cost layout needs support points and the squared "
+                    "Euclidean cost (cost = NULL)");
   long long tot = 0;
   for (int m = 0; m < d->M; ++m) {
     if (d->S[m] < 1)
@@ -198,6 +211,9 @@ size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c) {
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
+  if (h->gen_cost && c.kind != 2)
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "the generated cost layout runs on the cluster kernel (kind 2)");
   if (c.kind == 2) {  // one column per thread-block cluster
     if (c.vec != 2 && c.vec != 4 && c.vec != 8 && c.vec != 16)
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
@@ -271,7 +287,7 @@ mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
 // for the ring kernel; R = 3600: 54 us against 81 us).
 mam_kernel_config default_config(const mam_problem* h) {
   const int ld4 = h->ld / 4;
-  if (h->ld > kMaxCtaR) {
+  if (h->ld > kMaxCtaR || h->gen_cost) {
     // Longer than one CTA holds: a cluster per column, the fewest CTAs whose
     // slices stay within 64 KB of w (several resident CTAs per SM), else 16.
     mam_kernel_config c{};
@@ -359,10 +375,11 @@ mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
   if (c.kind == 2) {
     const size_t smem = cluster_kernel_smem(h->ld, c.vec);
     int clusters = 1 << 30;
+    const int dt = h->gen_cost ? -1 : h->cost_dtype;  // -1: costs generated in the kernel
     for (int dg = 0; dg < 2; ++dg) {
-      MAM_CUDA(set_column_cluster_smem(h->cost_dtype, dg != 0, smem), "cudaFuncSetAttribute");
+      MAM_CUDA(set_column_cluster_smem(dt, dg != 0, smem), "cudaFuncSetAttribute");
       int n = 0;
-      MAM_CUDA(column_cluster_occupancy(h->cost_dtype, dg != 0, c.vec, c.threads, smem, &n),
+      MAM_CUDA(column_cluster_occupancy(dt, dg != 0, c.vec, c.threads, smem, &n),
                "cluster occupancy");
       clusters = std::min(clusters, n);
     }
@@ -452,6 +469,9 @@ ColArgs col_args(const mam_problem* h) {
   a.cost = h->cost;
   a.cost_col = h->cost_col;
   a.cmul = h->cmul;
+  a.gen_xi = h->gen_xi;
+  a.gen_zeta = h->gen_zeta;
+  a.gen_dim = h->dim;
   a.q = h->q;
   a.lam = h->lam;
   a.nact = h->nact;
@@ -557,8 +577,8 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
   }
   const ColArgs ca = col_args(h);
   MAM_CUDA(h->cfg.kind == 2
-               ? launch_column_cluster(h->cost_dtype, diag, h->cfg.vec, h->grid,
-                                       h->cfg.threads, h->smem, h->stream, ca)
+               ? launch_column_cluster(h->gen_cost ? -1 : h->cost_dtype, diag, h->cfg.vec,
+                                       h->grid, h->cfg.threads, h->smem, h->stream, ca)
            : h->cfg.kind == 1
                ? launch_column_ring(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
                                     h->smem, h->stream, ca)
@@ -568,7 +588,8 @@ mam_status launch_iteration(mam_problem* h, bool diag) {
   if (diag && h->nb > 1) {
     // Lower bound of every measure for the v^k the column step just used
     // (the fused value covers only the drawn bundle).
-    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->cost_col, h->cmul, h->q, h->delta32,
+    MAM_CUDA(launch_lb(h->cost_dtype, h->cost, h->cost_col, h->cmul, h->gen_xi, h->gen_zeta,
+                       h->q, h->delta32,
                        h->t_used, h->meas_prob,
                        h->rho_m, h->col_meas, h->T, h->R, h->ld,
                        h->capped ? 0.f : INFINITY, h->diag_lb,
@@ -700,6 +721,26 @@ mam_status reset_state(mam_problem* h) {
   return sync(h);
 }
 
+// Generated costs: FP32 copies of the points, the barycenter points as
+// coordinate planes [P][3][ld] (zero past dim and past R) and (x, y, z, eta)
+// per kept column.
+mam_status upload_gen_points(mam_problem* h) {
+  std::vector<float> xi(size_t(h->P) * 3 * h->ld, 0.f);
+  std::vector<float4> ze(size_t(h->T));
+  for (int p = 0; p < h->P; ++p)
+    for (int r = 0; r < h->R; ++r)
+      for (int k = 0; k < h->dim; ++k)
+        xi[(size_t(p) * 3 + k) * h->ld + r] =
+            float(h->xi_h[(size_t(p) * h->R + r) * h->dim + k]);
+  for (long long c = 0; c < h->T; ++c) {
+    float v[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < h->dim; ++k) v[k] = float(h->zeta_kept[size_t(c) * h->dim + k]);
+    ze[c] = make_float4(v[0], v[1], v[2], float(h->eta_h[h->meas_prob_h[h->col_meas_h[c]]]));
+  }
+  MAM_TRY(upload(h, h->gen_xi, xi.data(), xi.size()));
+  return upload(h, h->gen_zeta, ze.data(), ze.size());
+}
+
 static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
                               const mam_shard* shard = nullptr) {
   if (!out) return fail(nullptr, MAM_ERR_INVALID_ARG, "out is NULL");
@@ -768,6 +809,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   h->theta0_mode = d0.theta0_mode;
   h->diag_mode = d0.diag_mode;
   h->shared_cost = d0.cost_layout == MAM_COST_SHARED;
+  h->gen_cost = d0.cost_layout == MAM_COST_GENERATED;
   h->n_sup = h->shared_cost ? d0.S[0] : 0;
   h->nb = (n == 1 && d0.n_bundles > 1) ? d0.n_bundles : 1;
   h->seed = d0.seed;
@@ -854,6 +896,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
     h->prob_meas.push_back(h->Mtot);
     h->prob_cols.push_back(h->col_off.back());
     h->rho.push_back(d.rho);
+    h->eta_h.push_back(d.eta);
     h->gamma.push_back(d.gamma);
     h->Qa.push_back(Qa);
   }
@@ -909,11 +952,14 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   if ((s = dalloc(h, &(ptr), (count), (what))) != MAM_OK) return bail(s)
   ALLOC(h->theta, Tld, "plans theta");
   void* costp = nullptr;
-  {
+  if (!h->gen_cost) {
     const size_t ncost = h->shared_cost ? size_t(h->n_sup) * h->ld : Tld;
     char* cp = nullptr;
     ALLOC(cp, ncost * cost_elem_size(h->cost_dtype), "costs");
     costp = cp;
+  } else {
+    ALLOC(h->gen_xi, size_t(h->P) * 3 * h->ld, "points (fp32)");
+    ALLOC(h->gen_zeta, size_t(h->T), "support points (fp32)");
   }
   h->cost = costp;
   ALLOC(h->q, size_t(h->T), "weights");
@@ -975,7 +1021,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   std::vector<float> rho_m(h->Mtot), irho_m(h->Mtot), cmul(h->Mtot, 1.f);
   for (int m = 0; m < h->Mtot; ++m) {
     rho_m[m] = float(h->rho[h->meas_prob_h[m]]);
-    const double a = h->shared_cost ? alpha_m[m] : 1.0;
+    const double a = (h->shared_cost || h->gen_cost) ? alpha_m[m] : 1.0;
     irho_m[m] = float(a / h->rho[h->meas_prob_h[m]]);
     cmul[m] = float(a);
   }
@@ -1044,6 +1090,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   if ((s = upload(h, h->col_off_d, h->col_off.data(), h->col_off.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->prob_cols_d, h->prob_cols.data(), h->prob_cols.size())) != MAM_OK) return bail(s);
   if ((s = upload(h, h->col_meas, col_meas.data(), col_meas.size())) != MAM_OK) return bail(s);
+  h->col_meas_h = col_meas;
   if (!h->bundle_cum.empty() &&
       (s = upload(h, h->bundle_cum_d, h->bundle_cum.data(), h->bundle_cum.size())) != MAM_OK)
     return bail(s);
@@ -1100,7 +1147,9 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
         }
         e = cudaMemcpy(zeta_d, zk.data(), sizeof(double) * zk.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { s = cuda_fail(h, e, "zeta upload"); break; }
-        if (h->shared_cost)  // one matrix C over the common support (xi is shared too)
+        if (h->gen_cost)  // nothing stored: the kernels compute c from the points
+          e = cudaSuccess;
+        else if (h->shared_cost)  // one matrix C over the common support (xi is shared too)
           e = i == 0 ? launch_build_cost(h->cost_dtype, h->cost, xi_d, h->sup_zeta_d, nullptr,
                                          h->sup_meas_d, h->sup_alpha_d, h->sup_eta_d, 0,
                                          h->n_sup, h->R, h->ld, h->dim, h->stream)
@@ -1147,6 +1196,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
     if (s != MAM_OK) return bail(s);
   }
 
+  if (h->gen_cost && (s = upload_gen_points(h)) != MAM_OK) return bail(s);
   if ((s = apply_config(h, default_config(h))) != MAM_OK) return bail(s);
   if ((s = reset_state(h)) != MAM_OK) return bail(s);
   *out = h;
@@ -1349,6 +1399,8 @@ mam_status mam_update_support(mam_problem* h, double* xi_out) {
   a.delta32 = h->delta32;
   a.inv_rho = h->irho_m;
   a.cost_col = h->cost_col;
+  a.gen_xi = h->gen_xi;
+  a.gen_zeta = h->gen_zeta;
   a.alpha = h->alpha_d;
   a.zeta = h->zeta_dev;
   a.acc = h->sup_acc;
@@ -1363,7 +1415,15 @@ mam_status mam_update_support(mam_problem* h, double* xi_out) {
   a.ld = h->ld;
   a.dim = h->dim;
   MAM_CUDA(launch_support_step(h->cost_dtype, a, h->xi_dev, h->stream), "support step");
-  // The costs of the new support (FP64, rounded to the storage type).
+  // The costs of the new support (FP64, rounded to the storage type; with
+  // generated costs, the FP32 copy of the new support).
+  if (h->gen_cost) {
+    MAM_CUDA(cudaMemcpyAsync(h->xi_h.data(), h->xi_dev, sizeof(double) * h->xi_h.size(),
+                             cudaMemcpyDeviceToHost, h->stream),
+             "read");
+    MAM_TRY(sync(h));
+    MAM_TRY(upload_gen_points(h));
+  } else
   MAM_CUDA(h->shared_cost
                ? launch_build_cost(h->cost_dtype, h->cost, h->xi_dev, h->sup_zeta_d, nullptr,
                                    h->sup_meas_d, h->sup_alpha_d, h->sup_eta_d, 0, h->n_sup,

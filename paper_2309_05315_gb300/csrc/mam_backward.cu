@@ -10,6 +10,11 @@
 // applies the reverse step of each iteration in reverse order
 // (mam_backward_kernels.cu).  Memory: (K / ckpt_every + 1) state snapshots
 // plus (ckpt_every + 1) active-set masks of one bit per plan entry.
+// With ckpt_every = 0 (automatic), when the masks of all K steps (K bits per
+// plan entry) fit in a quarter of the free device memory,
+// mam_forward_record keeps them from the forward pass itself, and
+// mam_backward applies the reverse steps directly: no segment is restored or
+// recomputed.  Otherwise (or with an explicit ckpt_every) it checkpoints.
 #include "mam.h"
 #include "mam_handle.h"
 #include "mam_internal.h"
@@ -28,6 +33,8 @@ struct BackwardState {
   size_t snap_bytes = 0;
   std::vector<char*> snaps;  // [nseg + 1]
   std::vector<long long> snap_iter, snap_diag_iter;
+  bool all_masks = false;         // the masks of all K steps are kept (no recomputation)
+  unsigned* mask_all = nullptr;   // [K][T][mw] active sets of every step (all_masks)
   unsigned* mask_seg = nullptr;   // [ck][T][mw] active sets of the segment's steps
   unsigned* mask_next = nullptr;  // [T][mw] active sets of the step after the segment
   float* stored = nullptr;   // [T][ld]
@@ -128,9 +135,10 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   if (h->P != 1) return fail(h, MAM_ERR_INVALID_ARG, "differentiation needs a single problem");
   if (h->sharded)
     return fail(h, MAM_ERR_INVALID_ARG, "differentiation is not offered for sharded problems");
-  if (h->ld > kMaxCtaR)  // the cluster kernel does not record active sets
+  if (h->ld > kMaxCtaR || h->cfg.kind == 2)  // the cluster kernel records no active sets
     return fail(h, MAM_ERR_INVALID_ARG,
-                "differentiation needs columns of at most " + std::to_string(kMaxCtaR) + " rows");
+                "differentiation needs columns of at most " + std::to_string(kMaxCtaR) +
+                    " rows and a one-CTA or one-warp column kernel (kind 0 or 1)");
   if (h->capped)
     return fail(h, MAM_ERR_INVALID_ARG,
                 "differentiation needs columns that carry their mass (capped = 0)");
@@ -141,6 +149,7 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   if (h->theta0_mode != 0 && h->theta0_mode != 1)
     return fail(h, MAM_ERR_INVALID_ARG, "theta0_mode must be 0 or 1");
   if (K < 1) return fail(h, MAM_ERR_INVALID_ARG, "K must be >= 1");
+  const bool automatic = ckpt_every == 0;
   if (ckpt_every == 0) ckpt_every = std::max(1, int(std::lround(std::sqrt(double(K)))));
   if (ckpt_every < 1 || ckpt_every > K)
     return fail(h, MAM_ERR_INVALID_ARG, "ckpt_every must be in 1..K (0 = about sqrt(K))");
@@ -159,11 +168,25 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
   const size_t MR = size_t(h->Mtot) * h->R;
   const int dim = std::max(1, h->dim);
   mam_status s = MAM_OK;
-  for (int i = 0; i <= b->nseg && s == MAM_OK; ++i)
-    s = balloc(h, b, &b->snaps[i], b->snap_bytes, "state snapshot");
   const size_t Tm = size_t(h->T) * ((h->ld + 31) / 32);
-  if (s == MAM_OK) s = balloc(h, b, &b->mask_seg, Tm * b->ck, "active sets");
-  if (s == MAM_OK) s = balloc(h, b, &b->mask_next, Tm, "active sets");
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    b->all_masks = automatic && size_t(K) * Tm * sizeof(unsigned) <= free_b / 4;
+  }
+  // Keeping every step's masks needs only the first and the last state.
+  for (int i = 0; i <= b->nseg && s == MAM_OK; ++i)
+    if (!b->all_masks || i == 0 || i == b->nseg)
+      s = balloc(h, b, &b->snaps[i], b->snap_bytes, "state snapshot");
+  if (b->all_masks) {
+    if (s == MAM_OK) s = balloc(h, b, &b->mask_all, Tm * size_t(K), "active sets");
+  } else {
+    if (s == MAM_OK) s = balloc(h, b, &b->mask_seg, Tm * b->ck, "active sets");
+    if (s == MAM_OK) s = balloc(h, b, &b->mask_next, Tm, "active sets");
+  }
   if (s == MAM_OK) s = balloc(h, b, &b->stored, Tl, "adjoint plan");
   if (s == MAM_OK) s = balloc(h, b, &b->pend, MR, "adjoint marginals");
   // chunks of at most kBwdChunk consecutive columns of one measure
@@ -206,6 +229,19 @@ mam_status mam_forward_record(mam_problem* h, int32_t K, int32_t ckpt_every) {
                         cudaMemcpyHostToDevice),
              "xi upload");
   BWD_TRY(reset_state(h));
+  if (b->all_masks) {
+    // The forward kernels record every step's active sets as they go.
+    BWD_TRY(snapshot(h, 0));
+    for (int k = 0; k < K; ++k) {
+      h->amask = b->mask_all + Tm * size_t(k);
+      const mam_status st = launch_iteration(h, false);
+      h->amask = nullptr;
+      BWD_TRY(st);
+    }
+    h->iter += K;
+    BWD_TRY(snapshot(h, b->nseg));
+    return sync(h);
+  }
   for (int seg = 0; seg < b->nseg; ++seg) {
     BWD_TRY(snapshot(h, seg));
     const int L = std::min(b->ck, K - seg * b->ck);
@@ -277,7 +313,13 @@ mam_status mam_backward(mam_problem* h, const double* grad_p, double* grad_q,
   A.mw = (h->ld + 31) / 32;
   const size_t Tm = size_t(h->T) * A.mw;
   bool have_next = false;  // the step after the segment exists (its sets are in mask_next)
-  for (int seg = b->nseg - 1; seg >= 0; --seg) {
+  if (b->all_masks)
+    for (int k = b->K - 1; k >= 0; --k) {
+      A.am = b->mask_all + Tm * size_t(k);
+      A.nm = k + 1 < b->K ? b->mask_all + Tm * size_t(k + 1) : nullptr;
+      BWD_CUDA(launch_bwd_step(b->nchunks, h->stream, A), "adjoint step");
+    }
+  for (int seg = b->all_masks ? -1 : b->nseg - 1; seg >= 0; --seg) {
     BWD_TRY(restore(h, seg));
     const int L = std::min(b->ck, b->K - seg * b->ck);
     // Re-run the segment; the column kernels record each step's active sets.

@@ -84,16 +84,25 @@ __global__ void __launch_bounds__(kBwdWarps * 32) bwd_column_kernel(const BwdArg
     const unsigned* nm = A.nm ? A.nm + size_t(col) * mw : nullptr;
     float* st = A.stored + size_t(col) * ld;
     // mean of thetabar' over the active set; the stored part is zero off the
-    // next step's active set
+    // next step's active set.  Active sets are sparse: the lanes load 32 mask
+    // words at a time and the warp visits only the nonzero ones (a ballot).
     float s1 = 0.f, na = 0.f;
-#pragma unroll 4
-    for (int v = 0; v < mw; ++v) {
-      const unsigned a = am[v];
-      if (a & bit) {
-        const int r = 32 * v + lane;
-        const float so = (nm && (nm[v] & bit)) ? st[r] : 0.f;
-        s1 += so + pd_s[r];
-        na += 1.f;
+    for (int v0 = 0; v0 < mw; v0 += 32) {
+      const bool in = v0 + lane < mw;
+      const unsigned aw = in ? am[v0 + lane] : 0u;
+      const unsigned bw = (in && nm) ? nm[v0 + lane] : 0u;
+      unsigned live = __ballot_sync(0xffffffffu, aw != 0u);
+      while (live) {
+        const int j = __ffs(live) - 1;
+        live &= live - 1;
+        const unsigned a = __shfl_sync(0xffffffffu, aw, j);
+        const unsigned b = __shfl_sync(0xffffffffu, bw, j);
+        if (a & bit) {
+          const int r = 32 * (v0 + j) + lane;
+          const float so = (b & bit) ? st[r] : 0.f;
+          s1 += so + pd_s[r];
+          na += 1.f;
+        }
       }
     }
 #pragma unroll
@@ -106,21 +115,31 @@ __global__ void __launch_bounds__(kBwdWarps * 32) bwd_column_kernel(const BwdArg
 #pragma unroll
     for (int k = 0; k < 3; ++k)
       if (k < dim) zs[k] = float(A.zeta[size_t(col) * dim + k]);
-    // wbar on the active set; zeros where the stored part was nonzero
-#pragma unroll 4
-    for (int v = 0; v < mw; ++v) {
-      const unsigned a = am[v], b = nm ? nm[v] : 0u;
-      if ((a | b) & bit) {
-        const int r = 32 * v + lane;
-        if (a & bit) {
-          const float so = (b & bit) ? st[r] : 0.f;
-          const float wb = (so + pd_s[r]) - mean;
-          st[r] = wb;
+    // wbar on the active set; zeros where the stored part was nonzero (the
+    // words of either set, visited as above)
+    for (int v0 = 0; v0 < mw; v0 += 32) {
+      const bool in = v0 + lane < mw;
+      const unsigned aw = in ? am[v0 + lane] : 0u;
+      const unsigned bw = (in && nm) ? nm[v0 + lane] : 0u;
+      unsigned live = __ballot_sync(0xffffffffu, (aw | bw) != 0u);
+      while (live) {
+        const int j = __ffs(live) - 1;
+        live &= live - 1;
+        const unsigned a = __shfl_sync(0xffffffffu, aw, j);
+        const unsigned b = __shfl_sync(0xffffffffu, bw, j);
+        if ((a | b) & bit) {
+          const int r = 32 * (v0 + j) + lane;
+          if (a & bit) {
+            const float so = (b & bit) ? st[r] : 0.f;
+            const float wb = (so + pd_s[r]) - mean;
+            st[r] = wb;
 #pragma unroll
-          for (int k = 0; k < 3; ++k)
-            if (k < dim) zx[k] = fmaf(wb, float(__ldg(A.xi + size_t(r) * dim + k)) - zs[k], zx[k]);
-        } else {
-          st[r] = 0.f;
+            for (int k = 0; k < 3; ++k)
+              if (k < dim)
+                zx[k] = fmaf(wb, float(__ldg(A.xi + size_t(r) * dim + k)) - zs[k], zx[k]);
+          } else {
+            st[r] = 0.f;
+          }
         }
       }
     }

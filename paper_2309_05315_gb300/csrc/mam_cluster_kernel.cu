@@ -129,7 +129,36 @@ constexpr int kClUnroll = 4;     // float4 groups a thread loads before using an
 // Every thread issues the loads of kClUnroll groups (theta, c and d: 12
 // independent 16-byte loads) before it uses any, so that a CTA keeps about
 // 50 KB in flight.
-template <typename CT, bool DIAG>
+// GEN: c is not read but computed as ||xi_r - zeta_s||^2 - eta in FP32 from
+// the points (the generated cost layout; CT is unused then).
+// xg: the problem's coordinate planes [3][ld]; one float4 per coordinate
+// covers the group's 4 rows.
+template <typename CT, bool DIAG, bool GEN>
+__device__ __forceinline__ float4 cost4(const ColArgs& A, const CT* c_g, const float* xg,
+                                        float4 zg, long long r, int R, int g) {
+  if (!GEN) return load_cost4<CT>(c_g, g);
+  const int ld = A.ld;
+  const float zc[3] = {zg.x, zg.y, zg.z};
+  // all three planes, independent loads issued together (planes past dim
+  // hold zeros, as does zeta there)
+  float4 x[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) x[k] = __ldg(reinterpret_cast<const float4*>(xg + size_t(k) * ld + r));
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float dx = x[k].x - zc[k], dy = x[k].y - zc[k], dz = x[k].z - zc[k],
+                dw = x[k].w - zc[k];
+    s.x = fmaf(dx, dx, s.x);
+    s.y = fmaf(dy, dy, s.y);
+    s.z = fmaf(dz, dz, s.z);
+    s.w = fmaf(dw, dw, s.w);
+  }
+  return make_float4(r < R ? s.x - zg.w : INFINITY, r + 1 < R ? s.y - zg.w : INFINITY,
+                     r + 2 < R ? s.z - zg.w : INFINITY, r + 3 < R ? s.w - zg.w : INFINITY);
+}
+
+template <typename CT, bool DIAG, bool GEN>
 __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const ColArgs A, int rpc) {
   extern __shared__ __align__(16) float w_s[];
   __shared__ float4 red[2 * kRedSlots];
@@ -183,7 +212,9 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
     }
     const float* th_g = A.theta + size_t(col) * ld + r0;
     const long long ccol = A.cost_col ? (long long)A.cost_col[col] : col;
-    const CT* c_g = static_cast<const CT*>(A.cost) + size_t(ccol) * ld + r0;
+    const CT* c_g = GEN ? nullptr : static_cast<const CT*>(A.cost) + size_t(ccol) * ld + r0;
+    const float* xg = GEN ? A.gen_xi + size_t(A.meas_prob[m]) * 3 * ld : nullptr;
+    const float4 zg = GEN ? A.gen_zeta[col] : make_float4(0.f, 0.f, 0.f, 0.f);
     const bool pos = tau > 0.f;
     const bool warm = pos && (lam_prev == lam_prev);
     const float l0 = warm ? lam_prev : 0.f;
@@ -197,7 +228,7 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
         const int g = g0 + u * nt;
         if (g < ng) {
           th[u] = __ldg(reinterpret_cast<const float4*>(th_g) + g);
-          c[u] = load_cost4<CT>(c_g, g);
+          c[u] = cost4<CT, DIAG, GEN>(A, c_g, xg, zg, r0 + 4LL * g, R, g);
           dd[u] = __ldg(reinterpret_cast<const float4*>(dl + r0) + g);
         }
       }
@@ -321,7 +352,7 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
             atomicAdd(acc_m + rr + e, (unsigned long long)f32_to_i64_rn(pv[e] * fx));
         if (DIAG) {
           const float4 th = __ldg(reinterpret_cast<const float4*>(th_g) + g);
-          const float4 c = load_cost4<CT>(c_g, g);
+          const float4 c = cost4<CT, DIAG, GEN>(A, c_g, xg, zg, rr, R, g);
           const float thv[4] = {th.x, th.y, th.z, th.w};
           const float cv[4] = {cm * c.x, cm * c.y, cm * c.z, cm * c.w};
           const float ovv[4] = {ov.x, ov.y, ov.z, ov.w};
@@ -363,10 +394,10 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
   cluster_sync();  // no CTA leaves while a peer could still store into it
 }
 
-template <typename CT, bool DIAG>
+template <typename CT, bool DIAG, bool GEN>
 cudaError_t cluster_op(int op, int cs, int grid, int threads, size_t smem, cudaStream_t st,
                        const ColArgs* a, int rpc, int* occ) {
-  auto kern = column_cluster_kernel<CT, DIAG>;
+  auto kern = column_cluster_kernel<CT, DIAG, GEN>;
   if (op == 1) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
@@ -398,12 +429,16 @@ cudaError_t cluster_op(int op, int cs, int grid, int threads, size_t smem, cudaS
 template <typename CT>
 cudaError_t cluster_op_d(int op, bool diag, int cs, int grid, int threads, size_t smem,
                          cudaStream_t st, const ColArgs* a, int rpc, int* occ) {
-  return diag ? cluster_op<CT, true>(op, cs, grid, threads, smem, st, a, rpc, occ)
-              : cluster_op<CT, false>(op, cs, grid, threads, smem, st, a, rpc, occ);
+  return diag ? cluster_op<CT, true, false>(op, cs, grid, threads, smem, st, a, rpc, occ)
+              : cluster_op<CT, false, false>(op, cs, grid, threads, smem, st, a, rpc, occ);
 }
 
+// dt < 0: generated costs (no stored cost type).
 cudaError_t cluster_op_any(int dt, int op, bool diag, int cs, int grid, int threads,
                            size_t smem, cudaStream_t st, const ColArgs* a, int rpc, int* occ) {
+  if (dt < 0)
+    return diag ? cluster_op<float, true, true>(op, cs, grid, threads, smem, st, a, rpc, occ)
+                : cluster_op<float, false, true>(op, cs, grid, threads, smem, st, a, rpc, occ);
   switch (dt) {
     case 0: return cluster_op_d<float>(op, diag, cs, grid, threads, smem, st, a, rpc, occ);
     case 1: return cluster_op_d<__nv_bfloat16>(op, diag, cs, grid, threads, smem, st, a, rpc, occ);

@@ -222,6 +222,15 @@ __device__ __forceinline__ float i64_to_f32(long long v) {
   return fmaf(float(hi), 4294967296.f, float(lo));
 }
 
+// Generated cost ||xi_r - zeta_s||^2 - eta in FP32: xi from coordinate
+// planes [3][ld] (x, y, z), zeta as (x, y, z, eta); coordinates past dim are
+// 0 in both.
+__device__ __forceinline__ float gen_cost(const float* planes, int ld, int r, float4 zeta) {
+  const float dx = planes[r] - zeta.x, dy = planes[ld + r] - zeta.y,
+              dz = planes[2 * ld + r] - zeta.z;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx)) - zeta.w;
+}
+
 // floor(x * a / 2^62) for |x| < 2^63, 0 <= a <= 2^62 (exact): the product of
 // a fixed-point marginal and an averaging weight a_m held as round(a_m 2^62).
 __device__ __forceinline__ long long mul_q62(long long x, long long a) {

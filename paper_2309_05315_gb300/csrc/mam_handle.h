@@ -122,6 +122,13 @@ struct mam_problem {
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
 
+  // generated cost layout (MAM_COST_GENERATED): no stored cost
+  bool gen_cost = false;
+  float* gen_xi = nullptr;     // [P][3][ld] FP32 coordinate planes (x, y, z)
+  float4* gen_zeta = nullptr;  // [T] (x, y, z, eta) FP32
+  std::vector<double> eta_h;   // [P] eta of each problem
+  std::vector<int> col_meas_h; // [T] measure of each kept column
+
   // shared cost layout (MAM_COST_SHARED): one matrix C over the common support
   bool shared_cost = false;
   int n_sup = 0;                  // columns of C (points of the common support)
@@ -203,6 +210,7 @@ struct Piece {
 };
 std::vector<Piece> state_pieces(mam_problem* h);
 mam_status reset_state(mam_problem* h);
+mam_status upload_gen_points(mam_problem* h);
 
 // Measure-sharded problems (mam_shard.cu).
 int shard_blocks(const mam_problem* h);

@@ -34,6 +34,10 @@ struct ColArgs {
   const void* cost;          // [T][ld] costs (float / bf16 / half), or [S][ld] shared
   const int* cost_col;       // [T] cost column of each plan column (shared layout), or null
   const float* cmul;         // [Mtot] factor of the stored cost: alpha_m (shared), else 1
+  const float* gen_xi;       // generated costs: [P][3][ld] coordinate planes of xi
+                             // (x, y, z; planes past dim and rows past R are 0), else null
+  const float4* gen_zeta;    // generated costs: [T] points (x, y, z, eta) of the columns
+  int gen_dim;               // coordinates used (1..3)
   const float* q;            // [T] kept weights q_s (the simplex masses)
   float* lam;                // [T] last threshold lambda_s (NaN: none)
   float* nact;               // [T] active-set size at that threshold (0: none)
@@ -153,7 +157,8 @@ cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                cudaStream_t st);
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const int* cost_col,
-                      const float* cmul, const float* q,
+                      const float* cmul, const float* gen_xi, const float4* gen_zeta,
+                      const float* q,
                       const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,

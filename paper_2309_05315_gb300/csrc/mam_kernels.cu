@@ -717,8 +717,8 @@ __global__ void __launch_bounds__(256) diag_reduce_kernel(
 // One warp per column.
 template <typename CT>
 __global__ void __launch_bounds__(256) lb_kernel(
-    const CT* cost, const int* cost_col, const float* cmul, const float* q,
-    const float* delta32, const double* t_used,
+    const CT* cost, const int* cost_col, const float* cmul, const float* gen_xi,
+    const float4* gen_zeta, const float* q, const float* delta32, const double* t_used,
     const int* meas_prob, const float* rho, const int* col_meas, long long T,
     int R, int ld, float lb_cap, float* diag_lb) {
   const int lane = threadIdx.x & 31;
@@ -729,12 +729,16 @@ __global__ void __launch_bounds__(256) lb_kernel(
     const float tt = float(t_used[meas_prob[m]]);
     const float rh = rho[m];
     const float* dl = delta32 + size_t(m) * ld;
-    const CT* cc = cost + size_t(cost_col ? (long long)cost_col[col] : col) * ld;
+    const CT* cc = gen_xi ? nullptr
+                          : cost + size_t(cost_col ? (long long)cost_col[col] : col) * ld;
     const float cm = cmul[m];
+    const float* xg = gen_xi ? gen_xi + size_t(meas_prob[m]) * 3 * ld : nullptr;
+    const float4 zg = gen_xi ? gen_zeta[col] : make_float4(0.f, 0.f, 0.f, 0.f);
     float mn = INFINITY;
     for (int r = lane; r < R; r += 32) {
       float c;
-      if constexpr (sizeof(CT) == 4) c = float(cc[r]);
+      if (gen_xi) c = gen_cost(xg, ld, r, zg);
+      else if constexpr (sizeof(CT) == 4) c = float(cc[r]);
       else if constexpr (std::is_same<CT, __half>::value) c = __half2float(cc[r]);
       else c = __bfloat162float(cc[r]);
       mn = fminf(mn, cm * c - rh * __fmul_rn(tt, dl[r]));
@@ -907,7 +911,8 @@ cudaError_t launch_rowsum(const float* theta, const long long* col_off,
 }
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const int* cost_col,
-                      const float* cmul, const float* q,
+                      const float* cmul, const float* gen_xi, const float4* gen_zeta,
+                      const float* q,
                       const float* delta32, const double* t_used,
                       const int* meas_prob, const float* rho,
                       const int* col_meas, long long T, int R, int ld,
@@ -917,13 +922,13 @@ cudaError_t launch_lb(int cost_dtype, const void* cost, const int* cost_col,
   if (g < 1) g = 1;
   switch (cost_dtype) {
     case 0:
-      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), cost_col, cmul, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
+      lb_kernel<float><<<int(g), 256, 0, st>>>(static_cast<const float*>(cost), cost_col, cmul, gen_xi, gen_zeta, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     case 1:
-      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), cost_col, cmul, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
+      lb_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(cost), cost_col, cmul, gen_xi, gen_zeta, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     case 2:
-      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), cost_col, cmul, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
+      lb_kernel<__half><<<int(g), 256, 0, st>>>(static_cast<const __half*>(cost), cost_col, cmul, gen_xi, gen_zeta, q, delta32, t_used, meas_prob, rho, col_meas, T, R, ld, lb_cap, diag_lb);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -52,11 +52,14 @@ __global__ void __launch_bounds__(256) support_accumulate_kernel(const SupportAr
     const int m = A.col_meas[col];
     const float irho = A.inv_rho[m];
     const float* th = A.theta + size_t(col) * A.ld;
-    const CT* cc = static_cast<const CT*>(A.cost) +
-                   size_t(A.cost_col ? (long long)A.cost_col[col] : col) * A.ld;
+    const CT* cc = A.gen_xi ? nullptr
+                            : static_cast<const CT*>(A.cost) +
+                                  size_t(A.cost_col ? (long long)A.cost_col[col] : col) * A.ld;
+    const float4 zg = A.gen_xi ? A.gen_zeta[col] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float* dl = A.delta32 + size_t(m) * A.ld;
     auto w_at = [&](int r) {
-      return fmaf(-cost_at(cc, r), irho, fmaf(2.f, __fmul_rn(A.t, dl[r]), th[r]));
+      const float c = A.gen_xi ? gen_cost(A.gen_xi, A.ld, r, zg) : cost_at(cc, r);
+      return fmaf(-c, irho, fmaf(2.f, __fmul_rn(A.t, dl[r]), th[r]));
     };
     float mx = -INFINITY;
     for (int r = lane; r < R; r += 32) mx = fmaxf(mx, w_at(r));

@@ -10,6 +10,8 @@ struct SupportArgs {
   const float* theta;        // [T][ld]
   const void* cost;          // [T][ld] (float / bf16 / half), or [S][ld] shared
   const int* cost_col;       // [T] cost column of each plan column (shared), or null
+  const float* gen_xi;       // generated costs: [3][ld] coordinate planes of xi, else null
+  const float4* gen_zeta;    // generated costs: [T] (x, y, z, eta)
   const float* q;            // [T]
   const float* lam;          // [T] last thresholds (warm start; NaN: none)
   const int* col_meas;       // [T]

@@ -7,8 +7,12 @@ theta^0 (balanced, deterministic, t = 1), as a float64 tensor on the device
 of ``q``.  Its backward pass is libmam's reverse sweep (mam_forward_record /
 mam_backward): gradients w.r.t. the weights q (unpruned order, zero for zero
 weights), the support points zeta and the barycenter points xi.  The inputs
-are copied to the host for mam_create, which copies them again; torch only
-supplies memory.
+are copied to the host for mam_create, which copies them again (the C ABI
+takes host arrays there and for the gradients); torch supplies memory and
+the stream: the library's work is ordered on torch's current stream of the
+device, and p is copied device to device.  ``ckpt_every = 0`` lets the
+library keep every step's active sets when they fit (no recomputation in the
+backward pass).
 """
 from __future__ import annotations
 
@@ -40,9 +44,13 @@ class MamFunction(torch.autograd.Function):
     def forward(ctx, q, zeta, xi, S, alpha, rho=100.0, K=200, ckpt_every=20,
                 theta0="spread"):
         prob = _problem(q, zeta, xi, S, alpha, rho)
-        mam = Mam(prob, cost_dtype="f32", theta0=theta0, diag="never")
+        dev = q.device if q.is_cuda else torch.device("cuda")
+        # the library orders its work on torch's current stream of that device
+        stream = torch.cuda.current_stream(dev)
+        mam = Mam(prob, cost_dtype="f32", theta0=theta0, diag="never", stream=stream)
         mam.forward_record(int(K), int(ckpt_every))
-        p = torch.from_numpy(mam.barycenter()).to(q.device)
+        p = mam.barycenter_into(torch.empty(mam.R, dtype=torch.float64, device=dev))
+        p = p.to(q.device)
         ctx.mam = mam
         ctx.shapes = (q.shape, zeta.shape, xi.shape)
         ctx.devices = (q.device, zeta.device, xi.device)

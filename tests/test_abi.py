@@ -145,6 +145,14 @@ def test_shared_cost_layout_needs_one_support(L):
     d3.cost = cost.ctypes.data_as(C.POINTER(C.c_double))
     assert L.mam_create(C.byref(d3), C.byref(h)) == 1
     assert b"cost = NULL" in L.mam_last_error(None)
-    d4, keep4 = make_desc(cost_layout=2)
+    d4, keep4 = make_desc(cost_layout=3)
     assert L.mam_create(C.byref(d4), C.byref(h)) == 1
     assert b"cost_layout" in L.mam_last_error(None)
+
+
+def test_generated_and_shared_layouts_need_positive_alpha(L):
+    d, keep = make_desc(cost_layout=2)
+    keep["alpha"][:] = [1.0, 0.0]
+    h = C.c_void_p()
+    assert L.mam_create(C.byref(d), C.byref(h)) == 1
+    assert b"alpha_m > 0" in L.mam_last_error(None)

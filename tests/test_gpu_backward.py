@@ -84,6 +84,25 @@ def test_checkpoint_interval_does_not_change_gradients(Mam):
             np.testing.assert_array_equal(a, b)
 
 
+def test_all_masks_mode_equals_checkpointing(Mam):
+    """ckpt_every = 0 keeps every step's active sets from the forward pass
+    (no recomputation); the gradients are bit for bit those of the
+    checkpointed sweep, and the state afterwards is the one after K steps."""
+    prob = config4(grid=24, M=4)
+    K = 30
+    ref = gpu_grads(Mam, prob, K, 7)
+    out = gpu_grads(Mam, prob, K, 0)
+    for a, b in zip(ref, out):
+        np.testing.assert_array_equal(a, b)
+    with Mam(prob, diag="never") as g:
+        g.forward_record(K, 0)
+        g.backward(np.ones(g.R))
+        th = g.theta()
+    with Mam(prob, diag="never") as g:
+        g.step(K)
+        np.testing.assert_array_equal(g.theta(), th)
+
+
 def test_state_restored_after_backward(Mam):
     prob = config4(grid=16, M=3)
     with Mam(prob, diag="never") as g:
