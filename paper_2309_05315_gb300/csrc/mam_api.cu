@@ -515,7 +515,7 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   a.prob_meas = h->prob_meas_d;
   a.S = h->S_d;
   a.inv_S = h->invS_f;
-  a.inv_SF = h->invSF_d;
+  a.inv_SFd = h->invSF_d;
   a.a_q = h->a_q_d;
   a.a = h->a_d;
   a.inv_Sd = h->invS_d;
@@ -1073,11 +1073,12 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
     if ((s = upload(h, h->Sd_d, Sd.data(), Sd.size())) != MAM_OK) return bail(s);
     // (pageable sources: the copy has taken the data when the call returns)
     if ((s = upload(h, h->invS_d, iS.data(), iS.size())) != MAM_OK) return bail(s);
-    std::vector<float> iSf(h->Mtot), iSF(h->Mtot);
+    std::vector<float> iSf(h->Mtot);
+    std::vector<double> iSF(h->Mtot);
     std::vector<long long> aq(h->Mtot);
     for (int m = 0; m < h->Mtot; ++m) {
       iSf[m] = float(iS[m]);
-      iSF[m] = float(iS[m] / h->fx_scale);
+      iSF[m] = iS[m] / h->fx_scale;  // F = 2^e: exact
       aq[m] = std::llround(std::ldexp(h->a[m], 62));
     }
     if ((s = upload(h, h->invS_f, iSf.data(), iSf.size())) != MAM_OK) return bail(s);

@@ -287,6 +287,15 @@ __device__ double t_from_blocks(const double* blk, int nblk, double rho,
   return double(__fdiv_rn(float(gamma), rD));
 }
 
+// The shift delta_r = (p_r - p^(m)_r) / S_m in FP32 from the exact
+// fixed-point difference (p - p^(m)) F and 1 / (S_m F) in FP64: one FP64
+// product, then one rounding to FP32.  (Rounding 1 / (S_m F) to FP32 instead
+// would give every row of measure m the same relative error in every
+// iteration, a bias that the iterates accumulate.)
+__device__ __forceinline__ float shift_f32(long long dfx, double inv_SFd) {
+  return __double2float_rn(double(dfx) * inv_SFd);
+}
+
 // ------------------------------------------------------- packed FP32 pairs
 
 // Blackwell executes two FP32 lanes per instruction for add/sub/fma on

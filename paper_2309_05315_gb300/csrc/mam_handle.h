@@ -89,7 +89,7 @@ struct mam_problem {
   double* Sd_d = nullptr;
   double* invS_d = nullptr;
   float* invS_f = nullptr;
-  float* invSF_d = nullptr;
+  double* invSF_d = nullptr;
   long long* a_q_d = nullptr;
   int* prob_meas_d = nullptr;
   double* rho_d = nullptr;

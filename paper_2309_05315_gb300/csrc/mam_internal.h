@@ -86,7 +86,7 @@ struct AvgArgs {
   const int* prob_meas;      // [P+1] first measure of each problem
   const int* S;              // [Mtot] pruned support sizes S_m
   const float* inv_S;        // [Mtot] 1 / S_m
-  const float* inv_SF;       // [Mtot] 1 / (S_m F)
+  const double* inv_SFd;     // [Mtot] 1 / (S_m F) in FP64 (the shifts' one product)
   const long long* a_q;      // [Mtot] round(a_m 2^62), weights of eq. (pr)
   const double* a;           // [Mtot] a_m (diagnostics)
   const double* inv_Sd;      // [Mtot] 1 / S_m in FP64 (diagnostics)

@@ -529,9 +529,9 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
     for (int k = 0; k < kAvgKeep; ++k) {
       if (k >= nk) break;
       const int m = mb + k * SL;
-      const float df = i64_to_f32(p_fx - pmr[k]);  // (p - p^(m)) F
-      A.delta32[size_t(m) * A.ld + r] = df * __ldg(A.inv_SF + m);
-      const float dv = df * A.fx_inv_f;
+      const long long dfx = p_fx - pmr[k];  // (p - p^(m)) F, exact
+      A.delta32[size_t(m) * A.ld + r] = shift_f32(dfx, __ldg(A.inv_SFd + m));
+      const float dv = i64_to_f32(dfx) * A.fx_inv_f;
       e = fmaf(dv * dv, __ldg(A.inv_S + m), e);
       if (diag) {
         const double dh = ph - A.phat[size_t(m) * A.R + r];
@@ -541,9 +541,9 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
     for (int k = kAvgKeep; k < nk; ++k) {
       const int m = mb + k * SL;
       const size_t o = size_t(m) * A.R + r;
-      const float df = i64_to_f32(p_fx - A.pm[o]);
-      A.delta32[size_t(m) * A.ld + r] = df * A.inv_SF[m];
-      const float dv = df * A.fx_inv_f;
+      const long long dfx = p_fx - A.pm[o];
+      A.delta32[size_t(m) * A.ld + r] = shift_f32(dfx, A.inv_SFd[m]);
+      const float dv = i64_to_f32(dfx) * A.fx_inv_f;
       e = fmaf(dv * dv, A.inv_S[m], e);
       if (diag) {
         const double dh = ph - A.phat[o];

@@ -81,9 +81,9 @@ __global__ void __launch_bounds__(kShardThreads)
     const double ph = A.diag ? phat_sum[r] : 0.0;
     for (int m = 0; m < Mloc; ++m) {
       const size_t o = size_t(m) * A.R + r;
-      const float df = i64_to_f32(p_fx - A.pm[o]);  // (p - p^(m)) F
-      A.delta32[size_t(m) * A.ld + r] = df * A.inv_SF[m];
-      const float dv = df * A.fx_inv_f;
+      const long long dfx = p_fx - A.pm[o];  // (p - p^(m)) F, exact
+      A.delta32[size_t(m) * A.ld + r] = shift_f32(dfx, A.inv_SFd[m]);
+      const float dv = i64_to_f32(dfx) * A.fx_inv_f;
       e = fmaf(dv * dv, A.inv_S[m], e);
       if (A.diag) {
         const double dh = ph - A.phat[o];

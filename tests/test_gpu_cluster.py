@@ -9,7 +9,7 @@ memory) against the FP64 oracle (Algorithm 1).
 * By default on the free-support grid of ten 60x60 images
   (R = 591^2 = 349281, Theorem 1), where one column needs 16 CTAs: a
   two-measure problem against the oracle's trajectory and its support step
-  (Prop. 4), and the full nested-ellipse problem (2.2e9 plan entries) by
+  (Prop. 4), and the full nested-ellipse problem (3.56e9 plan entries) by
   sampled columns one step ahead, the row sums of the new plans and the
   barycenter.
 """
@@ -132,7 +132,7 @@ def test_long_columns_support_step(Mam):
 
 def test_free_support_grid_full_size_sampled_columns(Mam):
     """Ten nested-ellipse images on their free-support grid (R = 349281,
-    6356 kept columns, 2.2e9 plan entries): after 20 iterations, sampled
+    10185 kept columns, 3.56e9 plan entries): after 20 iterations, sampled
     columns of one more step against FP64 projections of the same input
     state, the Step 3 row sums of one measure's new plans, and p (eq. pr)."""
     prob = config2_free_support()

@@ -103,13 +103,17 @@ def gaussian_blobs_image(rng, K, n_blobs, centre_lo, centre_hi, sig_lo, sig_hi,
     return img
 
 
-def nested_ellipses_image(rng, K=60, s_range=(600, 1500), max_tries=10000):
-    """2-3 concentric elliptical rings, 2 px wide, uniform intensity.
+def nested_ellipses_image(rng, K=60, s_range=(600, 1500), width=(2.0, 6.0),
+                          max_tries=10000):
+    """2-3 concentric elliptical rings, uniform intensity.
 
     A pixel is on when its distance to a ring, measured along the ray from the
-    shared centre, is below 1 px.  Images are redrawn until the number of
-    nonzero pixels falls in s_range (the shape of the paper's nested-ellipse
-    data, Section 6.1).
+    shared centre, is below half the ring width; the width is drawn once per
+    image from U[width].  Images are redrawn until the number of nonzero
+    pixels falls in s_range (the shape of the paper's nested-ellipse data,
+    Section 6.1).  On a 60x60 grid rings 2 px wide hold at most about 700
+    pixels, so the width range reaches up to 6 px for the supports to span
+    s_range.
     """
     I, J = _pixel_coords(K)
     for _ in range(max_tries):
@@ -117,6 +121,7 @@ def nested_ellipses_image(rng, K=60, s_range=(600, 1500), max_tries=10000):
         ci, cj = rng.uniform(22, 38, size=2)
         a, b = rng.uniform(14, 28, size=2)
         phi = rng.uniform(0, np.pi)
+        half = 0.5 * rng.uniform(*width)
         x, y = I - ci, J - cj
         u = np.cos(phi) * x + np.sin(phi) * y
         v = -np.sin(phi) * x + np.cos(phi) * y
@@ -126,7 +131,7 @@ def nested_ellipses_image(rng, K=60, s_range=(600, 1500), max_tries=10000):
         for scale in (1.0, 0.72, 0.45)[:n_rings]:
             aa, bb = a * scale, b * scale
             r_ell = aa * bb / np.sqrt((bb * np.cos(ang)) ** 2 + (aa * np.sin(ang)) ** 2)
-            img[np.abs(rad - r_ell) < 1.0] = 1.0
+            img[np.abs(rad - r_ell) < half] = 1.0
         s = int((img > 0).sum())
         if s_range[0] <= s <= s_range[1]:
             return img
