@@ -179,9 +179,14 @@ typedef struct {
 } mam_objective_t;
 
 /* Create a problem: validates, prunes zero-weight columns, builds the cost
- * on the device, sets theta^0 and the Step 0 marginals.  On failure *out is
- * NULL and nothing is leaked.  Cites: eq. (HugeLP), Section 4.3, Alg. 1
- * Step 0. */
+ * on the device, sets theta^0 and the Step 0 marginals.  With randomized
+ * index sets (n_bundles > 1) it also primes the stored thresholds: every
+ * index set is projected once from theta^0 and only the thresholds are kept
+ * (the state is reset to theta^0), so that a column's first visit starts its
+ * threshold search from a nearby value instead of the cold bracket; the
+ * iterates are those of Algorithm 1 from theta^0 either way.  On failure
+ * *out is NULL and nothing is leaked.  Cites: eq. (HugeLP), Section 4.3,
+ * Alg. 1 Step 0, Remark 2. */
 mam_status mam_create(const mam_desc* desc, mam_problem** out);
 
 /* ---------------------------------------------------------------------

@@ -343,7 +343,12 @@ mam_kernel_config default_config(const mam_problem* h) {
     }
   }
   best.ctas_per_sm = 0;
-  best.bisect_depth = 4;
+  // Cold starts (no stored threshold) go straight to Newton from the
+  // bracket's lower end: measured on the 100-measure unbalanced workload from
+  // a fresh state, the first 5 steps take 8.1 ms with no bisection against
+  // 9.3 ms with 4 steps, the next 20 steps 19.5 against 20.0 ms, and the same
+  // afterwards (R = 3600: no difference).
+  best.bisect_depth = 0;
   best.kind = 0;
   // Two stages overlap the next column's copy with this one's search; one
   // stage frees the shared memory for more resident CTAs, whose columns hide
@@ -569,22 +574,25 @@ static mam_status prof_event(mam_problem* h, cudaEvent_t* ev) {
   return MAM_OK;
 }
 
+// The column step of the configured kind with arguments ca.
+static cudaError_t launch_column_step(mam_problem* h, const ColArgs& ca, bool diag) {
+  return h->cfg.kind == 2
+             ? launch_column_cluster(h->gen_cost ? -1 : h->cost_dtype, diag, h->cfg.vec,
+                                     h->grid, h->cfg.threads, h->smem, h->stream, ca)
+         : h->cfg.kind == 1
+             ? launch_column_ring(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
+                                  h->smem, h->stream, ca)
+             : launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
+                             h->smem, h->stream, ca);
+}
+
 mam_status launch_iteration(mam_problem* h, bool diag) {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (h->profiling) {
     for (auto& e : ev) MAM_TRY(prof_event(h, &e));
     MAM_CUDA(cudaEventRecord(ev[0], h->stream), "cudaEventRecord");
   }
-  const ColArgs ca = col_args(h);
-  MAM_CUDA(h->cfg.kind == 2
-               ? launch_column_cluster(h->gen_cost ? -1 : h->cost_dtype, diag, h->cfg.vec,
-                                       h->grid, h->cfg.threads, h->smem, h->stream, ca)
-           : h->cfg.kind == 1
-               ? launch_column_ring(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
-                                    h->smem, h->stream, ca)
-               : launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
-                               h->smem, h->stream, ca),
-           "column kernel launch");
+  MAM_CUDA(launch_column_step(h, col_args(h), diag), "column kernel launch");
   if (diag && h->nb > 1) {
     // Lower bound of every measure for the v^k the column step just used
     // (the fused value covers only the drawn bundle).
@@ -719,6 +727,43 @@ mam_status reset_state(mam_problem* h) {
   h->iter = 0;
   h->diag_iter = -1;
   return sync(h);
+}
+
+// Randomized index sets (Remark 2): a column's first visit can come many
+// iterations after creation, and without a stored threshold its projection
+// starts with the cold search (bracket, bisection, Newton passes).  Prime the
+// thresholds: project every index set once from theta^0 (exact projections
+// of w = theta^0 + 2 t d^0 - c / rho), keep only the thresholds, and reset
+// everything else to the state of theta^0.  The iterates are those of
+// Algorithm 1 from theta^0 either way; only the starting points of the
+// threshold searches change.  One index set needs no priming: its first
+// iteration is that pass.
+mam_status prime_thresholds(mam_problem* h) {
+  if (h->nb <= 1 || h->index_sets.size() < 2) return MAM_OK;
+  for (size_t i = 0; i < h->index_sets.size(); ++i) {
+    ColArgs a = col_args(h);
+    a.sched = h->sched_d + i;  // with one draw, index set 0 of this schedule
+    a.draw.nb = 1;
+    a.amask = nullptr;
+    MAM_CUDA(launch_column_step(h, a, false), "threshold priming");
+  }
+  float* keep = nullptr;
+  MAM_CUDA(cudaMalloc(&keep, sizeof(float) * size_t(h->T)), "cudaMalloc (thresholds)");
+  mam_status s = MAM_OK;
+  cudaError_t e = cudaMemcpyAsync(keep, h->lam, sizeof(float) * size_t(h->T),
+                                  cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) s = cuda_fail(h, e, "threshold copy");
+  if (s == MAM_OK) s = reset_state(h);
+  if (s == MAM_OK) {
+    e = cudaMemcpyAsync(h->lam, keep, sizeof(float) * size_t(h->T), cudaMemcpyDeviceToDevice,
+                        h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(h->passes, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) s = cuda_fail(h, e, "threshold copy");
+  }
+  cudaFree(keep);
+  return s;
 }
 
 // Generated costs: FP32 copies of the points, the barycenter points as
@@ -1200,6 +1245,7 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   if (h->gen_cost && (s = upload_gen_points(h)) != MAM_OK) return bail(s);
   if ((s = apply_config(h, default_config(h))) != MAM_OK) return bail(s);
   if ((s = reset_state(h)) != MAM_OK) return bail(s);
+  if ((s = prime_thresholds(h)) != MAM_OK) return bail(s);
   *out = h;
   return MAM_OK;
 }
