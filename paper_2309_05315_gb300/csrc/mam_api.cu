@@ -701,8 +701,8 @@ mam_status reset_state(mam_problem* h) {
   MAM_CUDA(launch_init_theta(h->theta, h->lam, h->nact, h->q64, h->T, h->R, h->ld,
                              h->theta0_mode, h->stream),
            "init kernel");
-  MAM_CUDA(launch_rowsum(h->theta, h->col_off_d, h->Mtot, h->R, h->ld, h->fx_scale, h->pm,
-                         h->stream),
+  MAM_CUDA(launch_rowsum_theta0(h->q64, h->col_off_d, h->Mtot, h->R, h->theta0_mode,
+                                h->fx_scale, h->pm, h->stream),
            "rowsum kernel");
   const size_t MR = size_t(h->Mtot) * h->R;
   MAM_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * h->P * h->R, h->stream), "memset");

@@ -147,9 +147,8 @@ cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
 cudaError_t launch_init_theta(float* theta, float* lam, float* nact, const double* q,
                               long long T, int R, int ld, int mode,
                               cudaStream_t st);
-cudaError_t launch_rowsum(const float* theta, const long long* col_off,
-                          int Mtot, int R, int ld, double fx_scale, long long* pm,
-                          cudaStream_t st);
+cudaError_t launch_rowsum_theta0(const double* q, const long long* col_off, int Mtot, int R,
+                                 int mode, double fx_scale, long long* pm, cudaStream_t st);
 cudaError_t launch_diag_reduce(const float* wc, const float* lb,
                                const float* res, const long long* prob_cols,
                                const Sched* sched, Draw draw,

@@ -585,88 +585,6 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgArgs A) {
 
 // --------------------------------------------------------- other kernels
 
-// c_rs = alpha_m * ||xi_r - zeta_s||^2 (eq. HugeLP) or alpha_m * C_rs,
-// computed in FP64 without contraction, rounded to FP32, then to the storage
-// type (round to nearest even).  Padding rows R..ld-1 get +inf.  zeta and gen hold the
-// columns col0 .. col0+ncols-1 only.
-template <typename CT>
-__device__ __forceinline__ CT to_cost(float x);
-template <>
-__device__ __forceinline__ float to_cost<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_cost<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
-}
-template <>
-__device__ __forceinline__ __half to_cost<__half>(float x) {
-  return __float2half_rn(x);
-}
-
-template <typename CT>
-__global__ void build_cost_kernel(CT* cost, const double* xi,
-                                  const double* zeta, const double* gen,
-                                  const int* col_meas, const double* alpha,
-                                  const double* eta, long long col0,
-                                  long long ncols, int R, int ld, int dim) {
-  const long long n = ncols * ld;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long jc = i / ld;
-    const int r = int(i - jc * ld);
-    const long long col = col0 + jc;
-    double c = INFINITY;  // padding rows: w = -inf, never active
-    if (r < R) {
-      const double al = alpha[col_meas[col]];
-      const double et = eta ? eta[col_meas[col]] : 0.0;
-      if (gen) {
-        c = __dmul_rn(al, __dadd_rn(gen[jc * R + r], -et));
-      } else {
-        double acc = 0.0;
-        for (int k = 0; k < dim; ++k) {
-          const double df = __dadd_rn(zeta[jc * dim + k], -xi[size_t(r) * dim + k]);
-          acc = __dadd_rn(acc, __dmul_rn(df, df));
-        }
-        c = __dmul_rn(al, __dadd_rn(acc, -et));
-      }
-    }
-    cost[size_t(col) * ld + r] = to_cost<CT>(__double2float_rn(c));
-  }
-}
-
-// theta^0 (Alg. 1 Step 0; "Initialization" leaves it arbitrary):
-// mode 0: theta_rs = q_s / R, mode 1: 0.  Padding rows are 0 and every
-// threshold starts unknown (NaN, active-set size 0).
-__global__ void init_theta_kernel(float* theta, float* lam, float* nact,
-                                  const double* q, long long T, int R, int ld,
-                                  int mode) {
-  const long long n = T * ld;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long col = i / ld;
-    const int r = int(i - col * ld);
-    float v = 0.f;
-    if (mode == 0 && r < R) v = float(q[col] / double(R));
-    theta[i] = v;
-    if (r == 0) {
-      lam[col] = __int_as_float(0x7fc00000);
-      nact[col] = 0.f;
-    }
-  }
-}
-
-// p^(m)_r F = F sum_s theta^(m)_rs, summed in FP64 and rounded once to the
-// 64-bit fixed point of the marginals (Alg. 1 Step 0).
-__global__ void rowsum_kernel(const float* theta, const long long* col_off,
-                              int R, int ld, double fx_scale, long long* pm) {
-  const int m = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  double acc = 0.0;
-  for (long long c = col_off[m]; c < col_off[m + 1]; ++c)
-    acc += double(theta[size_t(c) * ld + r]);
-  pm[size_t(m) * R + r] = __double2ll_rn(acc * fx_scale);
-}
-
 // Sums of the per-column diagnostics of problem blockIdx.x, FP64, fixed
 // order: out[3*i] = sum wc, out[3*i+1] = sum lb, out[3*i+2] = sum res over
 // the columns of the last index set.
@@ -843,71 +761,6 @@ cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st) {
     default:
       return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
-                              const double* zeta, const double* gen_cost,
-                              const int* col_meas, const double* alpha,
-                              const double* eta, long long col0, long long ncols,
-                              int R, int ld, int dim, cudaStream_t st) {
-  const long long n = ncols * ld;
-  long long g = (n + 255) / 256;
-  if (g > 152 * 64) g = 152 * 64;
-  if (g < 1) g = 1;
-  switch (cost_dtype) {
-    case 0:
-      build_cost_kernel<float><<<int(g), 256, 0, st>>>(
-          static_cast<float*>(cost), xi, zeta, gen_cost, col_meas, alpha, eta,
-          col0, ncols, R, ld, dim);
-      break;
-    case 1:
-      build_cost_kernel<__nv_bfloat16><<<int(g), 256, 0, st>>>(
-          static_cast<__nv_bfloat16*>(cost), xi, zeta, gen_cost, col_meas,
-          alpha, eta, col0, ncols, R, ld, dim);
-      break;
-    case 2:
-      build_cost_kernel<__half><<<int(g), 256, 0, st>>>(
-          static_cast<__half*>(cost), xi, zeta, gen_cost, col_meas, alpha, eta,
-          col0, ncols, R, ld, dim);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_init_theta(float* theta, float* lam, float* nact,
-                              const double* q, long long T, int R, int ld,
-                              int mode, cudaStream_t st) {
-  const long long n = T * ld;
-  long long g = (n + 255) / 256;
-  if (g > 152 * 64) g = 152 * 64;
-  if (g < 1) g = 1;
-  init_theta_kernel<<<int(g), 256, 0, st>>>(theta, lam, nact, q, T, R, ld, mode);
-  return cudaGetLastError();
-}
-
-__global__ void fx_to_double_kernel(const long long* in, size_t n, double scale, double* out) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    out[i] = double(in[i]) * scale;
-}
-
-cudaError_t launch_fx_to_double(const long long* in, size_t n, double scale, double* out,
-                                cudaStream_t st) {
-  size_t g = (n + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  if (g < 1) g = 1;
-  fx_to_double_kernel<<<unsigned(g), 256, 0, st>>>(in, n, scale, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_rowsum(const float* theta, const long long* col_off,
-                          int Mtot, int R, int ld, double fx_scale, long long* pm,
-                          cudaStream_t st) {
-  rowsum_kernel<<<dim3((R + 127) / 128, Mtot), 128, 0, st>>>(theta, col_off, R,
-                                                             ld, fx_scale, pm);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_lb(int cost_dtype, const void* cost, const int* cost_col,
