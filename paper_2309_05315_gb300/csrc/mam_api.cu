@@ -479,7 +479,6 @@ ColArgs col_args(const mam_problem* h) {
   a.gen_dim = h->dim;
   a.q = h->q;
   a.lam = h->lam;
-  a.nact = h->nact;
   a.col_meas = h->col_meas;
   a.col_off = h->col_off_d;
   a.delta32 = h->delta32;
@@ -698,7 +697,7 @@ mam_status sync(mam_problem* h) {
 // ------------------------------------------------------------ creation
 
 mam_status reset_state(mam_problem* h) {
-  MAM_CUDA(launch_init_theta(h->theta, h->lam, h->nact, h->q64, h->T, h->R, h->ld,
+  MAM_CUDA(launch_init_theta(h->theta, h->lam, h->q64, h->T, h->R, h->ld,
                              h->theta0_mode, h->stream),
            "init kernel");
   MAM_CUDA(launch_rowsum_theta0(h->q64, h->col_off_d, h->Mtot, h->R, h->theta0_mode,
@@ -1019,7 +1018,6 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   h->avg_slices = choose_avg_slices(h);
   ALLOC(h->blk, size_t(h->P) * avg_blocks(h) * 4, "block sums");
   ALLOC(h->done, 1, "arrival counter");
-  ALLOC(h->nact, size_t(h->T), "active-set sizes");
   ALLOC(h->diag_wc, size_t(h->T), "diagnostics");
   ALLOC(h->diag_lb, size_t(h->T), "diagnostics");
   ALLOC(h->diag_res, size_t(h->T), "diagnostics");
@@ -1600,7 +1598,7 @@ struct StateHeader {
   int32_t P, Mtot, R, ld;
   int32_t bundle_cur, bundle_prev, pad0, pad1;
 };
-constexpr uint64_t kStateMagic = 0x324554415453414dull;  // "MASTATE2"
+constexpr uint64_t kStateMagic = 0x334554415453414dull;  // "MASTATE3"
 
 }  // namespace
 }  // extern "C"
@@ -1610,7 +1608,6 @@ std::vector<Piece> state_pieces(mam_problem* h) {
   const size_t MR = size_t(h->Mtot) * h->R;
   return {{h->theta, sizeof(float) * size_t(h->T) * h->ld},
           {h->lam, sizeof(float) * size_t(h->T)},
-          {h->nact, sizeof(float) * size_t(h->T)},
           {h->pm, sizeof(long long) * MR},
           {h->p, sizeof(double) * size_t(h->P) * h->R},
           {h->delta32, sizeof(float) * size_t(h->Mtot) * h->ld},

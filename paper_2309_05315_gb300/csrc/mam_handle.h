@@ -65,7 +65,6 @@ struct mam_problem {
   double* phat = nullptr;
   double* p = nullptr;
   double* t_used = nullptr;
-  float* nact = nullptr;
   unsigned* done = nullptr;
   double* blk = nullptr;
   float* diag_wc = nullptr;

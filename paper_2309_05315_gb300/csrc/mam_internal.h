@@ -40,7 +40,6 @@ struct ColArgs {
   int gen_dim;               // coordinates used (1..3)
   const float* q;            // [T] kept weights q_s (the simplex masses)
   float* lam;                // [T] last threshold lambda_s (NaN: none)
-  float* nact;               // [T] active-set size at that threshold (0: none)
   const int* col_meas;       // [T] measure of each column
   const long long* col_off;  // [Mtot+1] first column of each measure
   const float* delta32;      // [Mtot][ld] (p - p^(m)) / S_m in FP32, zero past R
@@ -144,7 +143,7 @@ cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const int* col_meas, const double* alpha,
                               const double* eta, long long col0, long long ncols,
                               int R, int ld, int dim, cudaStream_t st);
-cudaError_t launch_init_theta(float* theta, float* lam, float* nact, const double* q,
+cudaError_t launch_init_theta(float* theta, float* lam, const double* q,
                               long long T, int R, int ld, int mode,
                               cudaStream_t st);
 cudaError_t launch_rowsum_theta0(const double* q, const long long* col_off, int Mtot, int R,

@@ -68,8 +68,8 @@ __global__ void build_cost_kernel(CT* cost, const double* xi,
 
 // theta^0 (Alg. 1 Step 0; "Initialization" leaves it arbitrary):
 // mode 0: theta_rs = q_s / R, mode 1: 0.  Padding rows are 0 and every
-// threshold starts unknown (NaN, active-set size 0).
-__global__ void init_theta_kernel(float* theta, float* lam, float* nact,
+// threshold starts unknown (NaN).
+__global__ void init_theta_kernel(float* theta, float* lam,
                                   const double* q, long long T, int R, int ld,
                                   int mode) {
   // A block per column (grid-stride): q_s / R once per column, rows written
@@ -83,10 +83,7 @@ __global__ void init_theta_kernel(float* theta, float* lam, float* nact,
       th[g] = make_float4(r < R ? v : 0.f, r + 1 < R ? v : 0.f, r + 2 < R ? v : 0.f,
                           r + 3 < R ? v : 0.f);
     }
-    if (threadIdx.x == 0) {
-      lam[col] = __int_as_float(0x7fc00000);
-      nact[col] = 0.f;
-    }
+    if (threadIdx.x == 0) lam[col] = __int_as_float(0x7fc00000);
   }
 }
 
@@ -143,12 +140,12 @@ cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_theta(float* theta, float* lam, float* nact,
+cudaError_t launch_init_theta(float* theta, float* lam,
                               const double* q, long long T, int R, int ld,
                               int mode, cudaStream_t st) {
   long long g = T < 152 * 16 ? T : 152 * 16;
   if (g < 1) g = 1;
-  init_theta_kernel<<<int(g), ld >= 1024 ? 256 : 128, 0, st>>>(theta, lam, nact, q, T, R, ld,
+  init_theta_kernel<<<int(g), ld >= 1024 ? 256 : 128, 0, st>>>(theta, lam, q, T, R, ld,
                                                                  mode);
   return cudaGetLastError();
 }
