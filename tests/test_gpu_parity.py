@@ -157,6 +157,40 @@ def test_randomized_bundles(Mam):
     compare_trajectory(Mam, prob, 40, n_bundles=3, seed=1234, gamma=0.02)
 
 
+def _state_parts(gpu):
+    """theta [T][ld], the stored thresholds [T] and the iteration counter of a
+    mam_get_state blob (a 64-byte header, then theta and the thresholds)."""
+    blob = gpu.get_state()
+    T, ld = gpu.T, gpu.ld
+    it = int(np.frombuffer(blob, dtype=np.int64, count=1, offset=16)[0])
+    th = np.frombuffer(blob, dtype=np.float32, count=T * ld, offset=64).reshape(T, ld)
+    lam = np.frombuffer(blob, dtype=np.float32, count=T, offset=64 + 4 * T * ld)
+    return th, lam, it
+
+
+def test_thresholds_primed_for_bundles(Mam):
+    """With randomized index sets (Remark 2) creation primes the stored
+    thresholds: every kept column holds a finite threshold, while the iterate
+    is exactly theta^0 (the plans, the Step 0 marginals and p of the same
+    problem created without bundles, iteration 0).  With one index set the
+    thresholds stay unknown (NaN)."""
+    prob = tiny_problem(10, M=6, K=7, rho=15.0, masses=[0.5, 1, 1.5, 0.8, 1.2, 2.0])
+    with Mam(prob, n_bundles=3, seed=1234, gamma=0.02, diag="never") as primed, \
+         Mam(prob, n_bundles=1, gamma=0.02, diag="never") as plain:
+        th_a, lam_a, it_a = _state_parts(primed)
+        th_b, lam_b, it_b = _state_parts(plain)
+        assert it_a == 0 and it_b == 0
+        assert np.isfinite(lam_a).all()
+        assert np.isnan(lam_b).all()
+        np.testing.assert_array_equal(th_a, th_b)
+        prep = prepare(prob)
+        th0 = np.concatenate([np.repeat((q / prob.R).astype(np.float32)[:, None], prob.R, axis=1)
+                              for q in prep.q])
+        np.testing.assert_array_equal(th_a[:, :prob.R], th0)
+        np.testing.assert_array_equal(primed.marginals(), plain.marginals())
+        np.testing.assert_array_equal(primed.barycenter(), plain.barycenter())
+
+
 @pytest.mark.parametrize("cfg", [
     dict(kind=0, threads=32, vec=2, stages=2),
     dict(kind=0, threads=64, vec=1, stages=3),
