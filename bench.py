@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--cost-layout", default="per_column", choices=["per_column", "shared"],
                     help="shared: one cost matrix for measures on a common support")
     ap.add_argument("--cost-dtype", default=None, choices=["f32", "bf16", "f16"])
+    ap.add_argument("--plan-layout", default="dense", choices=["dense", "sparse"],
+                    help="sparse: plans stored as the (row, value) pairs of pihat "
+                         "(mam_desc.plan_layout)")
+    ap.add_argument("--sparse-slots", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
@@ -141,7 +145,9 @@ def peaks():
 # Sources of each column-step kernel: a recorded traffic figure holds only
 # while the hash of its kernel's sources is unchanged.
 KERNEL_SOURCES = {
-    "column_kernel": ("mam_kernels.cu", "mam_device.cuh", "mam_internal.h"),
+    "column_kernel": ("mam_column.cuh", "mam_kernels.cu", "mam_device.cuh", "mam_internal.h"),
+    "column_kernel_sparse": ("mam_column.cuh", "mam_sparse.cu", "mam_device.cuh",
+                             "mam_internal.h"),
     "column_ring_kernel": ("mam_warp_kernel.cu", "mam_device.cuh", "mam_internal.h"),
 }
 
@@ -291,6 +297,15 @@ def measure(idx, probs, cost_dtype, steps, warmup, local, dist=None, ext=None,
     # shared cost layout: the HBM traffic is theta (read and write); the one
     # cost matrix is read through L2
     bpe = 8 if ext.get("cost_layout") == "shared" else bytes_per_entry(cost_dtype)
+    sparse_note = None
+    if ext.get("plan_layout") == "sparse":
+        # cost bytes, plus a pair (8 B) read and written per active entry:
+        # the mean count of stored pairs after the window stands for the
+        # window's mean
+        cnt = np.frombuffer(gpu.get_state(), dtype=np.int32, count=gpu.T, offset=64)
+        act = float(cnt[cnt >= 0].mean()) if (cnt >= 0).any() else 0.0
+        bpe = (0 if ext.get("cost_layout") == "shared" else bpe - 8) + 16.0 * act / gpu.R
+        sparse_note = f"sparse plans: {act:.1f} stored pairs per column after the window"
     peak, peak_kind = peaks()
     achieved = win_entries * bpe / (col_ms / 1e3) / 1e9
     alg_launch = win_entries * bpe / max(n_timed, 1)
@@ -300,6 +315,9 @@ def measure(idx, probs, cost_dtype, steps, warmup, local, dist=None, ext=None,
                  "step on average, no flush")
     cfg["kernel_config"] = gpu.config()
     kernel = "column_ring_kernel" if cfg["kernel_config"]["kind"] == 1 else "column_kernel"
+    if sparse_note:
+        kernel = "column_kernel_sparse"
+        cfg["sparse_pairs"] = sparse_note
     traffic = ncu_traffic(cfg["workload"], win_entries / max(n_timed, 1), kernel)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
@@ -621,6 +639,9 @@ def main():
     ext = extension(args)
     if args.cost_layout != "per_column":
         ext["cost_layout"] = args.cost_layout
+    if args.plan_layout != "dense":
+        ext["plan_layout"] = args.plan_layout
+        ext["sparse_slots"] = args.sparse_slots
     head = measure(args.workload, probs, cost_dtype, args.steps, args.warmup, local, dist,
                    ext, args.autotune)
     if args.shard:

@@ -60,7 +60,9 @@ typedef enum {
   MAM_ERR_TIMEOUT = 5,
   MAM_ERR_STATE = 6,
   MAM_ERR_UNSUPPORTED = 7,
-  MAM_ERR_COMM = 8       /* the exchange callback of a sharded problem failed */
+  MAM_ERR_COMM = 8,      /* the exchange callback of a sharded problem failed */
+  MAM_ERR_CAPACITY = 9   /* sparse plan layout: a column's active set exceeded
+                            sparse_slots (the iterate is invalid)           */
 } mam_status;
 
 /* Storage type of the cost c (theta is always FP32; p, objective and
@@ -74,6 +76,9 @@ typedef enum {
   MAM_COST_SHARED = 1,
   MAM_COST_GENERATED = 2
 } mam_cost_layout;
+
+/* How the plans theta are stored (mam_desc.plan_layout). */
+typedef enum { MAM_PLAN_DENSE = 0, MAM_PLAN_SPARSE = 1 } mam_plan_layout;
 
 /* When the fused diagnostics (W-hat, dist_L(pi-hat), lower bound, residuals)
  * are computed. */
@@ -154,6 +159,30 @@ typedef struct {
                            kernel (kind 2) for every R; needs the squared
                            Euclidean cost (cost = NULL); cost_dtype is
                            ignored.  Reverse mode is not offered.            */
+  int32_t plan_layout;  /* 0 (MAM_PLAN_DENSE): theta stored as FP32 [T][ld].
+                           1 (MAM_PLAN_SPARSE): every step sets theta' = pihat
+                           - d (Alg. 1) with pihat zero off the column's active
+                           set and d one vector per measure, so a visited
+                           column is stored as the (row, value) pairs of its
+                           pihat (at most sparse_slots) and each measure keeps
+                           the d of its last visit; theta_rs = pihat_rs - d_r
+                           (one FP32 subtraction, the value the dense layout
+                           stores: the iterates are bit for bit the dense
+                           layout's).  Plan memory is 8 B x sparse_slots per
+                           column instead of 4 B x ld, and a column step reads
+                           its cost and pairs and writes pairs: the cost's
+                           HBM traffic plus 16 B per active entry.  Runs on
+                           the one-CTA-per-column kernel (kind 0, 1 stage,
+                           R <= 12288); not with the generated cost layout or
+                           the support step.  A column whose active set
+                           exceeds sparse_slots fails the step with
+                           MAM_ERR_CAPACITY; the handle is then unusable.
+                           mam_get_theta and mam_get_theta_range expand the
+                           plans on the device.  The order of a column's
+                           pairs in a state blob is not deterministic.       */
+  int32_t sparse_slots; /* sparse layout: pairs per column (even, 2..ld; 0:
+                           min(ld, 1024)).  Active sets are largest in the
+                           first iterations from theta^0.                    */
 } mam_desc;
 
 /* Diagnostics of the most recent diagnostic iteration k (all FP64). */

@@ -15,10 +15,11 @@ LIB_PATH = os.path.join(_PKG, "libmam.so")
 MAM_OK = 0
 STATUS = {0: "MAM_OK", 1: "MAM_ERR_INVALID_ARG", 2: "MAM_ERR_CUDA", 3: "MAM_ERR_OOM",
           4: "MAM_ERR_NONFINITE", 5: "MAM_ERR_TIMEOUT", 6: "MAM_ERR_STATE",
-          7: "MAM_ERR_UNSUPPORTED", 8: "MAM_ERR_COMM"}
+          7: "MAM_ERR_UNSUPPORTED", 8: "MAM_ERR_COMM", 9: "MAM_ERR_CAPACITY"}
 COST_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 DIAG_MODES = {"last": 0, "never": 1, "every": 2}
 COST_LAYOUTS = {"per_column": 0, "shared": 1, "generated": 2}
+PLAN_LAYOUTS = {"dense": 0, "sparse": 1}
 
 
 class MamDesc(C.Structure):
@@ -34,7 +35,8 @@ class MamDesc(C.Structure):
                 ("cost_dtype", C.c_int32), ("theta0_mode", C.c_int32),
                 ("diag_mode", C.c_int32), ("stream", C.c_void_p),
                 ("eta", C.c_double), ("capped", C.c_int32),
-                ("cost_layout", C.c_int32)]
+                ("cost_layout", C.c_int32), ("plan_layout", C.c_int32),
+                ("sparse_slots", C.c_int32)]
 
 
 # int32 allreduce(void* buf, int64 count, int32 dtype, void* stream, void* user)

@@ -28,7 +28,9 @@ thread_local std::string g_last_error;
 mam_status fail(mam_problem* h, mam_status code, const std::string& msg) {
   if (h) {
     h->err = msg;
-    if (code == MAM_ERR_CUDA || code == MAM_ERR_TIMEOUT || code == MAM_ERR_COMM) h->failed = true;
+    if (code == MAM_ERR_CUDA || code == MAM_ERR_TIMEOUT || code == MAM_ERR_COMM ||
+        code == MAM_ERR_CAPACITY)
+      h->failed = true;
   } else {
     g_last_error = msg;
   }
@@ -110,6 +112,23 @@ mam_status validate(const mam_desc* d, int idx) {
       if (!(d->alpha[m] > 0))
         return fail(nullptr, MAM_ERR_INVALID_ARG,
                     p + "the shared and generated cost layouts need alpha_m > 0");
+  }
+  if (d->plan_layout != MAM_PLAN_DENSE && d->plan_layout != MAM_PLAN_SPARSE)
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "unknown plan_layout");
+  if (d->plan_layout == MAM_PLAN_SPARSE) {
+    if (d->cost_layout == MAM_COST_GENERATED)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  p + "the sparse plan layout does not run with the generated cost layout");
+    if ((d->R + 7) / 8 * 8 > kMaxCtaR)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  p + "the sparse plan layout needs R <= " + std::to_string(kMaxCtaR) +
+                      " (one CTA per column)");
+    if (d->sparse_slots != 0 &&
+        (d->sparse_slots < 2 || d->sparse_slots % 2 || d->sparse_slots > (d->R + 7) / 8 * 8))
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  p + "sparse_slots must be 0 or even in 2..round_up(R, 8)");
+  } else if (d->sparse_slots != 0) {
+    return fail(nullptr, MAM_ERR_INVALID_ARG, p + "sparse_slots needs the sparse plan layout");
   }
   if (d->cost_layout == MAM_COST_GENERATED && (d->cost || !d->zeta))
     return fail(nullptr, MAM_ERR_INVALID_ARG,
@@ -204,16 +223,24 @@ static mam_status sched_alloc(mam_problem* h, void** p, size_t bytes) {
 
 size_t column_smem_bytes(const mam_problem* h, const mam_kernel_config& c) {
   // Each stage holds one column padded to threads * vec * 4 elements.
+  // Sparse plans: one theta tile, and per stage the cost and the pair slots.
   const size_t tile = size_t(c.threads) * c.vec * 4;
-  return size_t(c.stages) * tile * (sizeof(float) + cost_elem_size(h->cost_dtype)) +
-         4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4) +
-         kRedSlots * sizeof(double) + tile * sizeof(float);
+  const size_t fixed = 4 * sizeof(uint64_t) + 2 * kRedSlots * sizeof(float4) +
+                       kRedSlots * sizeof(double) + tile * sizeof(float);
+  if (h->sparse)
+    return tile * sizeof(float) + size_t(c.stages) * tile * cost_elem_size(h->cost_dtype) +
+           size_t(c.stages) * h->sp_k * sizeof(int2) + fixed + 4 * sizeof(int);
+  return size_t(c.stages) * tile * (sizeof(float) + cost_elem_size(h->cost_dtype)) + fixed;
 }
 
 mam_status check_config(const mam_problem* h, const mam_kernel_config& c) {
   if (h->gen_cost && c.kind != 2)
     return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
                 "the generated cost layout runs on the cluster kernel (kind 2)");
+  if (h->sparse && (c.kind != 0 || c.stages != 1))
+    return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
+                "the sparse plan layout runs on the one-CTA-per-column kernel (kind 0) "
+                "with 1 stage");
   if (c.kind == 2) {  // one column per thread-block cluster
     if (c.vec != 2 && c.vec != 4 && c.vec != 8 && c.vec != 16)
       return fail(const_cast<mam_problem*>(h), MAM_ERR_INVALID_ARG,
@@ -304,7 +331,7 @@ mam_kernel_config default_config(const mam_problem* h) {
     c.bisect_depth = 4;
     return c;
   }
-  if (h->ld <= 1024) {
+  if (h->ld <= 1024 && !h->sparse) {
     // The narrowest compiled width that covers the column, up to 12 ring
     // slots (as many as fit in shared memory) and one warp per slot.
     const int need = (ld4 + 31) / 32;
@@ -356,16 +383,20 @@ mam_kernel_config default_config(const mam_problem* h) {
   // stage at 4 CTAs/SM, 60-64 us with two at 2 CTAs/SM).  Take one stage
   // when it admits more CTAs per SM.
   int occ_by_stages[3] = {0, 0, 0};
-  for (int st = 1; st <= 2; ++st) {
+  for (int st = 1; st <= (h->sparse ? 1 : 2); ++st) {
     best.stages = st;
     const size_t smem = column_smem_bytes(h, best);
     int occ = 1 << 30;
     for (int dg = 0; dg < 2; ++dg) {
       int o = 0;
       if (smem > 232448 ||
-          set_column_smem(best.vec, h->cost_dtype, dg != 0, smem) != cudaSuccess ||
-          column_occupancy(best.vec, h->cost_dtype, dg != 0, best.threads, smem, &o) !=
-              cudaSuccess)
+          (h->sparse ? set_column_sparse_smem(best.vec, h->cost_dtype, dg != 0, smem)
+                     : set_column_smem(best.vec, h->cost_dtype, dg != 0, smem)) !=
+              cudaSuccess ||
+          (h->sparse ? column_sparse_occupancy(best.vec, h->cost_dtype, dg != 0, best.threads,
+                                               smem, &o)
+                     : column_occupancy(best.vec, h->cost_dtype, dg != 0, best.threads, smem,
+                                        &o)) != cudaSuccess)
         o = 0;
       occ = std::min(occ, o);
     }
@@ -418,17 +449,21 @@ mam_status apply_config(mam_problem* h, const mam_kernel_config& c) {
   const bool wk = c.kind == 1;
   const size_t smem = wk ? ring_kernel_smem(c.vec, c.stages, int(cost_elem_size(h->cost_dtype)))
                          : column_smem_bytes(h, c);
+  const bool sparse = h->sparse;
   for (int dg = 0; dg < 2; ++dg)
     MAM_CUDA(wk ? set_column_ring_smem(c.vec, h->cost_dtype, dg != 0, smem)
-                : set_column_smem(c.vec, h->cost_dtype, dg != 0, smem),
+             : sparse ? set_column_sparse_smem(c.vec, h->cost_dtype, dg != 0, smem)
+                  : set_column_smem(c.vec, h->cost_dtype, dg != 0, smem),
              "cudaFuncSetAttribute");
   int occ = 0;
   MAM_CUDA(wk ? column_ring_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ)
-              : column_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ),
+           : sparse ? column_sparse_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ)
+                : column_occupancy(c.vec, h->cost_dtype, true, c.threads, smem, &occ),
            "occupancy");
   int occ2 = 0;
   MAM_CUDA(wk ? column_ring_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2)
-              : column_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2),
+           : sparse ? column_sparse_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2)
+                : column_occupancy(c.vec, h->cost_dtype, false, c.threads, smem, &occ2),
            "occupancy");
   occ = std::min(occ, occ2);
   if (occ < 1)
@@ -509,6 +544,11 @@ ColArgs col_args(const mam_problem* h) {
   a.bisect_depth = h->cfg.bisect_depth;
   a.lam_floor = h->capped ? 0.f : -INFINITY;
   a.lb_cap = h->capped ? 0.f : INFINITY;
+  a.sp_cnt = h->sp_cnt;
+  a.sp_pairs = h->sp_pairs;
+  a.d_last = h->d_last;
+  a.th0 = h->th0;
+  a.sp_k = h->sp_k;
   return a;
 }
 
@@ -540,6 +580,7 @@ AvgArgs avg_args(const mam_problem* h, int reduce, int diag) {
   a.phat = h->phat;
   a.blk = h->blk;
   a.slices = h->avg_slices;
+  a.d_last = h->d_last;
   return a;
 }
 
@@ -581,6 +622,9 @@ static cudaError_t launch_column_step(mam_problem* h, const ColArgs& ca, bool di
          : h->cfg.kind == 1
              ? launch_column_ring(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
                                   h->smem, h->stream, ca)
+         : h->sparse
+             ? launch_column_sparse(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
+                                    h->smem, h->stream, ca)
              : launch_column(h->cfg.vec, h->cost_dtype, diag, h->grid, h->cfg.threads,
                              h->smem, h->stream, ca);
 }
@@ -683,6 +727,10 @@ mam_status check_device_error(mam_problem* h) {
   int e = 0;
   MAM_CUDA(cudaMemcpy(&e, h->err_d, sizeof(int), cudaMemcpyDeviceToHost),
            "error word read");
+  if (e == 2)
+    return fail(h, MAM_ERR_CAPACITY,
+                "sparse plan layout: a column's active set exceeded sparse_slots = " +
+                    std::to_string(h->sp_k) + " (the iterate is invalid)");
   if (e != 0)
     return fail(h, MAM_ERR_TIMEOUT,
                 "a device-side wait exceeded its bound (the iterate is invalid)");
@@ -697,9 +745,17 @@ mam_status sync(mam_problem* h) {
 // ------------------------------------------------------------ creation
 
 mam_status reset_state(mam_problem* h) {
-  MAM_CUDA(launch_init_theta(h->theta, h->lam, h->q64, h->T, h->R, h->ld,
-                             h->theta0_mode, h->stream),
-           "init kernel");
+  if (h->sparse) {
+    MAM_CUDA(launch_init_sparse(h->sp_cnt, h->th0, h->lam, h->q64, h->T, h->R,
+                                h->theta0_mode, h->stream),
+             "init kernel");
+    MAM_CUDA(cudaMemsetAsync(h->d_last, 0, sizeof(float) * size_t(h->Mtot) * h->ld, h->stream),
+             "memset");
+  } else {
+    MAM_CUDA(launch_init_theta(h->theta, h->lam, h->q64, h->T, h->R, h->ld,
+                               h->theta0_mode, h->stream),
+             "init kernel");
+  }
   MAM_CUDA(launch_rowsum_theta0(h->q64, h->col_off_d, h->Mtot, h->R, h->theta0_mode,
                                 h->fx_scale, h->pm, h->stream),
            "rowsum kernel");
@@ -809,6 +865,10 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
                   "and capped");
     if (descs[i].cost_layout != descs[0].cost_layout)
       return fail(nullptr, MAM_ERR_INVALID_ARG, "batched problems must share cost_layout");
+    if (descs[i].plan_layout != descs[0].plan_layout ||
+        descs[i].sparse_slots != descs[0].sparse_slots)
+      return fail(nullptr, MAM_ERR_INVALID_ARG,
+                  "batched problems must share plan_layout and sparse_slots");
     if (descs[0].cost_layout == MAM_COST_SHARED) {
       const size_t nx = size_t(descs[0].R) * descs[0].dim;
       const size_t nz = size_t(descs[0].S[0]) * descs[0].dim;
@@ -854,6 +914,8 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   h->diag_mode = d0.diag_mode;
   h->shared_cost = d0.cost_layout == MAM_COST_SHARED;
   h->gen_cost = d0.cost_layout == MAM_COST_GENERATED;
+  h->sparse = d0.plan_layout == MAM_PLAN_SPARSE;
+  h->sp_k = !h->sparse ? 0 : d0.sparse_slots > 0 ? d0.sparse_slots : std::min(h->ld, 1024);
   h->n_sup = h->shared_cost ? d0.S[0] : 0;
   h->nb = (n == 1 && d0.n_bundles > 1) ? d0.n_bundles : 1;
   h->seed = d0.seed;
@@ -994,7 +1056,14 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
   mam_status s = MAM_OK;
 #define ALLOC(ptr, count, what) \
   if ((s = dalloc(h, &(ptr), (count), (what))) != MAM_OK) return bail(s)
-  ALLOC(h->theta, Tld, "plans theta");
+  if (h->sparse) {
+    ALLOC(h->sp_cnt, size_t(h->T), "sparse plan counts");
+    ALLOC(h->sp_pairs, size_t(h->T) * h->sp_k, "sparse plan pairs");
+    ALLOC(h->d_last, size_t(h->Mtot) * h->ld, "shifts of the last visits");
+    ALLOC(h->th0, size_t(h->T), "theta^0 values");
+  } else {
+    ALLOC(h->theta, Tld, "plans theta");
+  }
   void* costp = nullptr;
   if (!h->gen_cost) {
     const size_t ncost = h->shared_cost ? size_t(h->n_sup) * h->ld : Tld;
@@ -1391,6 +1460,8 @@ mam_status mam_solve(mam_problem* h, int32_t max_iters, double gap_tol, double w
 
 mam_status mam_update_support(mam_problem* h, double* xi_out) {
   MAM_CHECK_HANDLE(h);
+  if (h->sparse)
+    return fail(h, MAM_ERR_UNSUPPORTED, "the support step needs the dense plan layout");
   if (h->P != 1) return fail(h, MAM_ERR_INVALID_ARG, "the support step needs a single problem");
   if (h->sharded)
     return fail(h, MAM_ERR_INVALID_ARG, "the support step is not offered for sharded problems");
@@ -1490,6 +1561,8 @@ mam_status mam_free_support(mam_problem* h, int32_t outer, int32_t inner_iters, 
   MAM_CHECK_HANDLE(h);
   if (outer < 0 || inner_iters < 0 || check_every < 1 || !(gap_tol >= 0))
     return fail(h, MAM_ERR_INVALID_ARG, "bad free-support arguments");
+  if (h->sparse)
+    return fail(h, MAM_ERR_UNSUPPORTED, "the support step needs the dense plan layout");
   if (h->sharded)
     return fail(h, MAM_ERR_INVALID_ARG, "the support step is not offered for sharded problems");
   int total = 0;
@@ -1541,9 +1614,37 @@ mam_status mam_get_marginals(mam_problem* h, double* pm_out, int32_t device_ptr)
   return MAM_OK;
 }
 
+// Sparse plans: theta of columns col0 .. col0 + ncols - 1, expanded on the
+// device in chunks of at most 64 MB and copied to the host.
+static mam_status get_theta_sparse(mam_problem* h, long long col0, long long ncols,
+                                   float* out) {
+  const long long chunk = std::max(1LL, (64LL << 20) / (4LL * h->R));
+  float* buf = nullptr;
+  MAM_CUDA(cudaMalloc(&buf, sizeof(float) * size_t(std::min(chunk, ncols)) * h->R),
+           "cudaMalloc (theta expansion)");
+  mam_status s = MAM_OK;
+  for (long long c = 0; c < ncols && s == MAM_OK; c += chunk) {
+    const long long n = std::min(chunk, ncols - c);
+    cudaError_t e = launch_expand_sparse(buf, col0 + c, n, h->sp_cnt, h->sp_pairs, h->sp_k,
+                                         h->d_last, h->th0, h->col_meas, h->R, h->ld,
+                                         h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + size_t(c) * h->R, buf, sizeof(float) * size_t(n) * h->R,
+                          cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) s = cuda_fail(h, e, "theta expansion");
+  }
+  cudaFree(buf);
+  return s != MAM_OK ? s : sync(h);
+}
+
 mam_status mam_get_theta(mam_problem* h, float* theta_out) {
   MAM_CHECK_HANDLE(h);
   if (!theta_out) return fail(h, MAM_ERR_INVALID_ARG, "theta_out is NULL");
+  if (h->sparse) {
+    MAM_TRY(sync(h));
+    return get_theta_sparse(h, 0, h->T, theta_out);
+  }
   MAM_CUDA(cudaMemcpy2DAsync(theta_out, sizeof(float) * h->R, h->theta,
                              sizeof(float) * h->ld, sizeof(float) * h->R, h->T,
                              cudaMemcpyDeviceToHost, h->stream),
@@ -1557,6 +1658,10 @@ mam_status mam_get_theta_range(mam_problem* h, int64_t col0, int64_t ncols, floa
   if (col0 < 0 || ncols < 0 || col0 + ncols > h->T)
     return fail(h, MAM_ERR_INVALID_ARG, "column range outside 0..T");
   if (ncols == 0) return MAM_OK;
+  if (h->sparse) {
+    MAM_TRY(sync(h));
+    return get_theta_sparse(h, col0, ncols, theta_out);
+  }
   MAM_CUDA(cudaMemcpy2DAsync(theta_out, sizeof(float) * h->R, h->theta + size_t(col0) * h->ld,
                              sizeof(float) * h->ld, sizeof(float) * h->R, size_t(ncols),
                              cudaMemcpyDeviceToHost, h->stream),
@@ -1596,7 +1701,7 @@ struct StateHeader {
   uint64_t magic;
   int64_t T, iter, diag_iter;
   int32_t P, Mtot, R, ld;
-  int32_t bundle_cur, bundle_prev, pad0, pad1;
+  int32_t bundle_cur, bundle_prev, plan_layout, sparse_slots;
 };
 constexpr uint64_t kStateMagic = 0x334554415453414dull;  // "MASTATE3"
 
@@ -1606,7 +1711,14 @@ constexpr uint64_t kStateMagic = 0x334554415453414dull;  // "MASTATE3"
 namespace mam {
 std::vector<Piece> state_pieces(mam_problem* h) {
   const size_t MR = size_t(h->Mtot) * h->R;
-  return {{h->theta, sizeof(float) * size_t(h->T) * h->ld},
+  std::vector<Piece> plans;
+  if (h->sparse)
+    plans = {{h->sp_cnt, sizeof(int) * size_t(h->T)},
+             {h->sp_pairs, sizeof(int2) * size_t(h->T) * h->sp_k},
+             {h->d_last, sizeof(float) * size_t(h->Mtot) * h->ld}};
+  else
+    plans = {{h->theta, sizeof(float) * size_t(h->T) * h->ld}};
+  std::vector<Piece> rest = {
           {h->lam, sizeof(float) * size_t(h->T)},
           {h->pm, sizeof(long long) * MR},
           {h->p, sizeof(double) * size_t(h->P) * h->R},
@@ -1619,6 +1731,8 @@ std::vector<Piece> state_pieces(mam_problem* h) {
           {h->diag_res, sizeof(float) * size_t(h->T)},
           {h->passes, sizeof(unsigned long long)},
           {h->iter_d, sizeof(long long)}};
+  plans.insert(plans.end(), rest.begin(), rest.end());
+  return plans;
 }
 }  // namespace mam
 
@@ -1645,6 +1759,8 @@ mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes) {
   hd.Mtot = h->Mtot;
   hd.R = h->R;
   hd.ld = h->ld;
+  hd.plan_layout = h->sparse ? MAM_PLAN_SPARSE : MAM_PLAN_DENSE;
+  hd.sparse_slots = h->sp_k;
   char* out = static_cast<char*>(buf);
   std::memcpy(out, &hd, sizeof(hd));
   size_t off = sizeof(hd);
@@ -1666,7 +1782,9 @@ mam_status mam_set_state(mam_problem* h, const void* buf, size_t bytes) {
   if (bytes < need) return fail(h, MAM_ERR_INVALID_ARG, "state buffer too small");
   std::memcpy(&hd, buf, sizeof(hd));
   if (hd.magic != kStateMagic || hd.T != h->T || hd.P != h->P || hd.Mtot != h->Mtot ||
-      hd.R != h->R || hd.ld != h->ld)
+      hd.R != h->R || hd.ld != h->ld ||
+      hd.plan_layout != (h->sparse ? MAM_PLAN_SPARSE : MAM_PLAN_DENSE) ||
+      hd.sparse_slots != h->sp_k)
     return fail(h, MAM_ERR_INVALID_ARG, "state does not belong to this problem");
   MAM_TRY(sync(h));
   const char* in = static_cast<const char*>(buf);

@@ -47,6 +47,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
       : "memory");
 }
 
+// Orders this thread's view of earlier generic-proxy shared-memory accesses
+// (made visible to it by a barrier) before its later async-proxy copies.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // One bulk copy global -> shared (sizes and addresses multiples of 16 B);
 // completion is reported as transaction bytes on `bar`.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src,

@@ -121,6 +121,15 @@ struct mam_problem {
   std::vector<cudaEvent_t> prof_events;
   size_t prof_used = 0;
 
+  // sparse plan layout (MAM_PLAN_SPARSE): theta = pihat - d_last with pihat
+  // held as pairs; no dense theta
+  bool sparse = false;
+  int sp_k = 0;               // pair slots per column (even)
+  int* sp_cnt = nullptr;      // [T] stored pairs of each column (-1: theta^0)
+  int2* sp_pairs = nullptr;   // [T][sp_k] (row, FP32 bits of pihat_r)
+  float* d_last = nullptr;    // [Mtot][ld] d of each measure's last column step
+  float* th0 = nullptr;       // [T] theta^0 of each column (rows < R)
+
   // generated cost layout (MAM_COST_GENERATED): no stored cost
   bool gen_cost = false;
   float* gen_xi = nullptr;     // [P][3][ld] FP32 coordinate planes (x, y, z)

@@ -30,7 +30,7 @@ struct Draw {
 // Arguments of the fused column kernel (Algorithm 1, Step 2, the Step 3
 // accumulation of row sums, t^k, and the fused diagnostics).
 struct ColArgs {
-  float* theta;              // [T][ld] plans, column-contiguous
+  float* theta;              // [T][ld] plans, column-contiguous (dense layout)
   const void* cost;          // [T][ld] costs (float / bf16 / half), or [S][ld] shared
   const int* cost_col;       // [T] cost column of each plan column (shared layout), or null
   const float* cmul;         // [Mtot] factor of the stored cost: alpha_m (shared), else 1
@@ -72,6 +72,12 @@ struct ColArgs {
                              // for capped columns (projection onto Delta_<=(q_s))
   float lb_cap;              // upper clamp of a column's lower-bound term per unit
                              // mass: +inf, or 0 for capped columns
+  // Sparse plan layout (theta = pihat - d_last, pihat as pairs; else unused)
+  int* sp_cnt;               // [T] stored pairs of each column (-1: theta^0)
+  int2* sp_pairs;            // [T][sp_k] (row, FP32 bits of pihat_r)
+  const float* d_last;       // [Mtot][ld] d of each measure's last column step
+  const float* th0;          // [T] theta^0 of each column on rows < R
+  int sp_k;                  // pair slots per column (even)
 };
 
 // Arguments of the averaging kernel (Algorithm 1, Step 3 completion, Step 1
@@ -106,6 +112,8 @@ struct AvgArgs {
   double* phat;              // [Mtot][R] row sums of pi-hat (DIAG)
   double* blk;               // [P][nblk][4] block sums: dist^2, dist_hat^2, |dp|^2
   int slices;                // measure slices per block (1, 2, 4, 8)
+  float* d_last;             // [Mtot][ld] sparse plans: d of each updated measure's
+                             // column step (written), else null
 };
 
 constexpr int kAvgThreads = 128;  // threads per averaging block: rows x measure slices
@@ -120,6 +128,18 @@ int column_max_threads(int nv);
 cudaError_t column_occupancy(int nv, int cost_dtype, bool diag, int threads,
                              size_t smem, int* blocks_per_sm);
 cudaError_t launch_average(const AvgArgs& a, int nblk, cudaStream_t st);
+// The sparse plan layout (mam_sparse.cu).
+cudaError_t launch_column_sparse(int nv, int cost_dtype, bool diag, int grid, int threads,
+                                 size_t smem, cudaStream_t st, const ColArgs& a);
+cudaError_t set_column_sparse_smem(int nv, int cost_dtype, bool diag, size_t smem);
+cudaError_t column_sparse_occupancy(int nv, int cost_dtype, bool diag, int threads,
+                                    size_t smem, int* blocks_per_sm);
+cudaError_t launch_init_sparse(int* cnt, float* th0, float* lam, const double* q,
+                               long long T, int R, int mode, cudaStream_t st);
+cudaError_t launch_expand_sparse(float* out, long long col0, long long ncols, const int* cnt,
+                                 const int2* pairs, int K, const float* d_last,
+                                 const float* th0, const int* col_meas, int R, int ld,
+                                 cudaStream_t st);
 // One warp per column with a shared-memory ring (mam_warp_kernel.cu).
 bool ring_kernel_has(int nv);
 int ring_kernel_max_threads(int nv);

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kShardThreads)
       A.acc[o] = 0ull;
       // the column kernel subtracted d = float(t delta) from every entry
       const float d_used = __fmul_rn(t_old, A.delta32[size_t(m) * A.ld + r]);
+      if (A.d_last) A.d_last[size_t(m) * A.ld + r] = d_used;  // sparse plans
       const long long d_fx = f32_to_i64_rn(d_used * A.fx_f);  // F = 2^e: exact scaling
       if (A.diag) A.phat[o] = double(sum_pihat) * A.fx_inv_scale;
       pmv = sum_pihat - (long long)A.S[m] * d_fx;

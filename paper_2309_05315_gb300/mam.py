@@ -26,7 +26,8 @@ class _DescKeep:
     """Owns the contiguous arrays a mam_desc points into."""
 
     def __init__(self, problem, cost_dtype, theta0_mode, diag_mode, n_bundles,
-                 seed, rho, gamma, stream, capped=False, eta=0.0, cost_layout="per_column"):
+                 seed, rho, gamma, stream, capped=False, eta=0.0, cost_layout="per_column",
+                 plan_layout="dense", sparse_slots=0):
         M = len(problem.q)
         xi = np.ascontiguousarray(problem.xi, dtype=np.float64)
         if xi.ndim == 1:
@@ -67,6 +68,8 @@ class _DescKeep:
         d.eta = float(eta)
         d.capped = 1 if capped else 0
         d.cost_layout = _capi.COST_LAYOUTS[cost_layout]
+        d.plan_layout = _capi.PLAN_LAYOUTS[plan_layout]
+        d.sparse_slots = int(sparse_slots)
         self.desc = d
 
 
@@ -83,9 +86,12 @@ class Mam:
                  seed: int = 0, rho: Optional[float] = None,
                  gamma: Optional[float] = None, stream=None,
                  capped: bool = False, eta: float = 0.0, shard=None,
-                 cost_layout: str = "per_column"):
+                 cost_layout: str = "per_column", plan_layout: str = "dense",
+                 sparse_slots: int = 0):
         """``cost_layout="shared"`` stores one cost matrix for measures on a
         common support (mam_desc.cost_layout).
+        ``plan_layout="sparse"`` stores each column's pihat as (row, value)
+        pairs, at most ``sparse_slots`` of them (mam_desc.plan_layout).
         ``shard=(m_begin, m_end, allreduce)`` creates this rank's part of a
         measure-sharded problem (mam_create_sharded); ``allreduce`` is a
         ctypes ``_capi.ALLREDUCE_FN`` (see ``paper_2309_05315_gb300.shard``),
@@ -100,7 +106,7 @@ class Mam:
         if stream is not None:
             st = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         keeps = [_DescKeep(p, cost_dtype, theta0, diag, n_bundles, seed, rho, gamma, st,
-                           capped, eta, cost_layout)
+                           capped, eta, cost_layout, plan_layout, sparse_slots)
                  for p in probs]
         self._h = C.c_void_p()
         self._shard = None
