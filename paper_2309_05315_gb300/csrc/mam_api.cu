@@ -841,6 +841,145 @@ mam_status upload_gen_points(mam_problem* h) {
   return upload(h, h->gen_zeta, ze.data(), ze.size());
 }
 
+// Distinct values of one coordinate, keyed by bit pattern, in order of first
+// appearance (open addressing); false once there are more than `limit`.
+static bool distinct_values(const double* v, size_t n, size_t stride, int limit,
+                            std::vector<double>& vals, std::vector<int>& idx) {
+  size_t cap = 64;
+  while (cap < 2 * size_t(limit)) cap <<= 1;
+  std::vector<uint64_t> key(cap);
+  std::vector<int> slot(cap, -1);
+  vals.clear();
+  idx.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t b;
+    std::memcpy(&b, v + i * stride, sizeof b);
+    size_t h = size_t((b ^ (b >> 29)) * 0x9E3779B97F4A7C15ull) & (cap - 1);
+    while (slot[h] >= 0 && key[h] != b) h = (h + 1) & (cap - 1);
+    if (slot[h] < 0) {
+      if (int(vals.size()) == limit) return false;
+      slot[h] = int(vals.size());
+      key[h] = b;
+      vals.push_back(v[i * stride]);
+    }
+    idx[i] = slot[h];
+  }
+  return true;
+}
+
+// Squared-Euclidean costs of columns c0 .. c0 + ncols - 1 through the
+// coordinate tables (CostTab) when every coordinate of xi and of the
+// columns' points takes few distinct values (pixel grids); *done stays false
+// otherwise and the direct kernel runs.  The tables hold the direct
+// formula's per-coordinate squares, so the costs are the same bit for bit.
+static mam_status build_cost_tabulated(mam_problem* h, const double* xi,
+                                       const std::vector<double>& zk, long long c0,
+                                       long long ncols, const long long* cols_d, bool* done) {
+  *done = false;
+  const int dim = h->dim, R = h->R;
+  constexpr int kLimit = 4096;  // distinct values per coordinate
+  std::vector<double> ux[3], uz[3];
+  std::vector<int> ixk[3], izk[3];
+  long long entries = 0;
+  for (int k = 0; k < dim; ++k) {
+    if (!distinct_values(xi + k, size_t(R), size_t(dim), kLimit, ux[k], ixk[k]) ||
+        !distinct_values(zk.data() + k, size_t(ncols), size_t(dim), kLimit, uz[k], izk[k]))
+      return MAM_OK;
+    entries += (long long)ux[k].size() * (long long)uz[k].size();
+  }
+  // worth it only when the tables are much smaller than the costs
+  if (entries > (1LL << 22) || entries * 16 > ncols * (long long)R) return MAM_OK;
+  CostTab tb{};
+  tb.dim = dim;
+  std::vector<int> ix(size_t(dim) * R), iz(size_t(ncols) * dim);
+  std::vector<double> vals;
+  long long off = 0;
+  for (int k = 0; k < dim; ++k) {
+    tb.off[k] = off;
+    tb.nx[k] = int(ux[k].size());
+    off += (long long)ux[k].size() * (long long)uz[k].size();
+    std::copy(ixk[k].begin(), ixk[k].end(), ix.begin() + size_t(k) * R);
+    for (long long c = 0; c < ncols; ++c) iz[size_t(c) * dim + k] = izk[k][c];
+  }
+  // one device block: [tables][value lists][ix][iz]
+  std::vector<size_t> vbeg(dim);
+  for (int k = 0; k < dim; ++k) {
+    vbeg[k] = vals.size();
+    vals.insert(vals.end(), uz[k].begin(), uz[k].end());
+    vals.insert(vals.end(), ux[k].begin(), ux[k].end());
+  }
+  const size_t b_tab = sizeof(double) * size_t(entries);
+  const size_t b_val = sizeof(double) * vals.size();
+  const size_t b_ix = sizeof(int) * ix.size(), b_iz = sizeof(int) * iz.size();
+  char* dev = nullptr;
+  MAM_CUDA(cudaMalloc(&dev, b_tab + b_val + b_ix + b_iz), "cudaMalloc (cost tables)");
+  double* tab = reinterpret_cast<double*>(dev);
+  double* dval = reinterpret_cast<double*>(dev + b_tab);
+  int* dix = reinterpret_cast<int*>(dev + b_tab + b_val);
+  int* diz = reinterpret_cast<int*>(dev + b_tab + b_val + b_ix);
+  cudaError_t e = cudaMemcpyAsync(dval, vals.data(), b_val, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dix, ix.data(), b_ix, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(diz, iz.data(), b_iz, cudaMemcpyHostToDevice, h->stream);
+  for (int k = 0; k < dim && e == cudaSuccess; ++k)
+    e = launch_sqdiff_table(tab + tb.off[k], dval + vbeg[k], int(uz[k].size()),
+                            dval + vbeg[k] + uz[k].size(), int(ux[k].size()), h->stream);
+  if (e == cudaSuccess)
+    e = launch_build_cost_tab(h->cost_dtype, h->cost, tab, tb, dix, diz, h->col_meas,
+                              h->alpha_d, h->eta_d, c0, ncols, R, h->ld, h->stream, cols_d);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // (pageable sources, then free)
+  cudaFree(dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tabulated cost kernel");
+  *done = true;
+  return MAM_OK;
+}
+
+// Columns c0 .. c1 - 1 whose cost columns repeat an earlier one: equal point
+// (bit for bit), alpha_m and eta give the same column.  reps: the columns to
+// build (global indices, first of each class); dst_src: (column, its class's
+// first column) for the others.
+static void repeated_cost_columns(const std::vector<double>& zk, int dim, long long c0,
+                                  long long c1, const std::vector<int>& col_meas,
+                                  const std::vector<double>& alpha_m,
+                                  const std::vector<double>& eta_m, std::vector<long long>& reps,
+                                  std::vector<long long>& dst_src) {
+  const long long n = c1 - c0;
+  const int w = dim + 2;
+  auto word = [&](long long j, int i) {
+    double v = i < dim ? zk[size_t(j) * dim + i]
+                       : (i == dim ? alpha_m[col_meas[c0 + j]] : eta_m[col_meas[c0 + j]]);
+    uint64_t b;
+    std::memcpy(&b, &v, sizeof b);
+    return b;
+  };
+  size_t cap = 64;
+  while (cap < 2 * size_t(n)) cap <<= 1;
+  std::vector<long long> slot(cap, -1);
+  reps.clear();
+  dst_src.clear();
+  for (long long j = 0; j < n; ++j) {
+    uint64_t hsh = 0x9E3779B97F4A7C15ull;
+    for (int i = 0; i < w; ++i) hsh = (hsh ^ word(j, i)) * 0xff51afd7ed558ccdull;
+    size_t s = size_t(hsh ^ (hsh >> 31)) & (cap - 1);
+    for (;; s = (s + 1) & (cap - 1)) {
+      const long long k = slot[s];
+      if (k < 0) {
+        slot[s] = j;
+        reps.push_back(c0 + j);
+        break;
+      }
+      bool same = true;
+      for (int i = 0; i < w && same; ++i) same = word(j, i) == word(k, i);
+      if (same) {
+        dst_src.push_back(c0 + j);
+        dst_src.push_back(c0 + k);
+        break;
+      }
+    }
+  }
+}
+
 static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
                               const mam_shard* shard = nullptr) {
   if (!out) return fail(nullptr, MAM_ERR_INVALID_ARG, "out is NULL");
@@ -1267,10 +1406,53 @@ static mam_status create_impl(int n, const mam_desc* descs, mam_problem** out,
                                          h->sup_meas_d, h->sup_alpha_d, h->sup_eta_d, 0,
                                          h->n_sup, h->R, h->ld, h->dim, h->stream)
                      : cudaSuccess;
-        else
-          e = launch_build_cost(h->cost_dtype, h->cost, xi_d, zeta_d, nullptr,
-                                h->col_meas, h->alpha_d, h->eta_d, c0, c1 - c0, h->R, h->ld,
-                                h->dim, h->stream);
+        else {
+          // Repeated columns (the same point in several measures of equal
+          // alpha_m and eta) are built once and copied.
+          std::vector<long long> reps, dst_src;
+          repeated_cost_columns(zk, d.dim, c0, c1, col_meas, alpha_m, eta_m, reps, dst_src);
+          std::vector<double> zr;
+          const std::vector<double>* zb = &zk;
+          long long* lists = nullptr;  // device: [reps][dst_src]
+          if (!dst_src.empty()) {
+            zr.resize(reps.size() * size_t(d.dim));
+            for (size_t j = 0; j < reps.size(); ++j)
+              for (int k = 0; k < d.dim; ++k)
+                zr[j * d.dim + k] = zk[size_t(reps[j] - c0) * d.dim + k];
+            zb = &zr;
+            e = cudaMalloc(&lists, sizeof(long long) * (reps.size() + dst_src.size()));
+            if (e == cudaSuccess)
+              e = cudaMemcpy(lists, reps.data(), sizeof(long long) * reps.size(),
+                             cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+              e = cudaMemcpy(lists + reps.size(), dst_src.data(),
+                             sizeof(long long) * dst_src.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+              e = cudaMemcpy(zeta_d, zr.data(), sizeof(double) * zr.size(),
+                             cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+              if (lists) cudaFree(lists);
+              s = cuda_fail(h, e, "cost column lists");
+              break;
+            }
+          }
+          const long long nb = (long long)reps.size();
+          bool tabulated = false;
+          s = build_cost_tabulated(h, d.xi, *zb, c0, nb, lists, &tabulated);
+          if (s == MAM_OK && !tabulated)
+            e = launch_build_cost(h->cost_dtype, h->cost, xi_d, zeta_d, nullptr, h->col_meas,
+                                  h->alpha_d, h->eta_d, c0, nb, h->R, h->ld, h->dim,
+                                  h->stream, lists);
+          if (s == MAM_OK && e == cudaSuccess && lists)
+            e = launch_copy_cost_columns(h->cost_dtype, h->cost, lists + reps.size(),
+                                         (long long)dst_src.size() / 2, h->ld, h->stream);
+          if (lists) {
+            const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+            if (e == cudaSuccess) e = e2;
+            cudaFree(lists);
+          }
+          if (s != MAM_OK) break;
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { s = cuda_fail(h, e, "cost kernel"); break; }
       } else {

@@ -158,11 +158,34 @@ cudaError_t launch_column_cluster(int cost_dtype, bool diag, int cs, int grid, i
 cudaError_t set_column_cluster_smem(int cost_dtype, bool diag, size_t smem);
 cudaError_t column_cluster_occupancy(int cost_dtype, bool diag, int cs, int threads,
                                      size_t smem, int* clusters);
+// Squared-Euclidean costs from per-coordinate tables (mam_setup.cu): when
+// the points take few distinct values per coordinate (pixel grids), the
+// table of coordinate k holds fl(fl(zv_u - xv_v)^2) for every pair of
+// distinct values, [nz_k][nx_k] from element off[k] of one FP64 buffer; a
+// cost entry is then the same FP64 sum of the same squares the direct formula
+// forms.
+struct CostTab {
+  int dim;
+  long long off[3];  // first element of each coordinate's table
+  int nx[3];         // distinct barycenter-point values of each coordinate
+};
+cudaError_t launch_sqdiff_table(double* tab, const double* uz, int nz, const double* ux,
+                                int nx, cudaStream_t st);
+// cols (optional): the columns to build, [ncols], in place of col0 + j.
+cudaError_t launch_build_cost_tab(int cost_dtype, void* cost, const double* tab,
+                                  const CostTab& tb, const int* ix, const int* iz,
+                                  const int* col_meas, const double* alpha, const double* eta,
+                                  long long col0, long long ncols, int R, int ld,
+                                  cudaStream_t st, const long long* cols = nullptr);
+// Copies cost column src to dst for every pair of dst_src [n][2].
+cudaError_t launch_copy_cost_columns(int cost_dtype, void* cost, const long long* dst_src,
+                                     long long n, int ld, cudaStream_t st);
 cudaError_t launch_build_cost(int cost_dtype, void* cost, const double* xi,
                               const double* zeta, const double* gen_cost,
                               const int* col_meas, const double* alpha,
                               const double* eta, long long col0, long long ncols,
-                              int R, int ld, int dim, cudaStream_t st);
+                              int R, int ld, int dim, cudaStream_t st,
+                              const long long* cols = nullptr);
 cudaError_t launch_init_theta(float* theta, float* lam, const double* q,
                               long long T, int R, int ld, int mode,
                               cudaStream_t st);

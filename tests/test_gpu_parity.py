@@ -135,6 +135,27 @@ def test_general_cost_matrix(Mam):
     compare_trajectory(Mam, prob, 30)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_tabulated_cost_equals_direct_formula(Mam, dtype):
+    """Pixel-grid points take few values per coordinate, so creation builds
+    the squared-Euclidean costs from per-coordinate tables of squares.  The
+    same problem given as a general cost matrix (the same FP64 operations,
+    d = z - x, d * d, the squares added in coordinate order, on the host) must
+    give bit-identical iterates."""
+    prob = tiny_problem(31, M=4, K=12, rho=20.0, density=0.8)
+    alt = copy.copy(prob)
+    xi = np.asarray(prob.xi, dtype=np.float64)
+    alt.cost = [(z[:, None, 0] - xi[None, :, 0]) ** 2 + (z[:, None, 1] - xi[None, :, 1]) ** 2
+                for z in (np.asarray(v, dtype=np.float64) for v in prob.zeta)]
+    with Mam(prob, cost_dtype=dtype, diag="never") as a, \
+         Mam(alt, cost_dtype=dtype, diag="never") as b:
+        for n in (1, 4, 15):
+            a.step(n)
+            b.step(n)
+            assert np.array_equal(a.theta(), b.theta())
+            assert np.array_equal(a.barycenter(), b.barycenter())
+
+
 def test_theta0_zero(Mam):
     compare_trajectory(Mam, tiny_problem(8, M=3, K=6, rho=10.0), 30, theta0="zero")
 
