@@ -296,6 +296,8 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
           nprev = -1.f;
           bracket = false;
         }
+        // (f, n) at lam, and min_r |w_r - lam| for the certificate of the
+        // Newton step from lam (a pass costs a cluster barrier)
         float4 u = make_float4(0.f, 0.f, INFINITY, -INFINITY);
         for (int g = tid; g < ng; g += nt) {
           const float4 w = w4[g];
@@ -304,6 +306,7 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
           for (int e = 0; e < 4; ++e) {
             u.x += fmaxf(xs[e], 0.f);
             u.y += xs[e] > 0.f ? 1.f : 0.f;
+            u.z = fminf(u.z, fabsf(xs[e]));
           }
         }
         const float4 tn = cred(u);
@@ -319,8 +322,11 @@ __global__ void __launch_bounds__(kClThreads, 2) column_cluster_kernel(const Col
           continue;
         }
         nprev = cnt;
-        lam = lam + (f - tau) / cnt;
+        const float dl = (f - tau) / cnt;
+        const float lam_from = lam;
+        lam = lam + dl;
         lam_fin = lam;  // used if the pass budget runs out (not expected)
+        if (newton_certified(tn.z, dl, lam_from)) break;  // the next pass would confirm lam
       }
     }
 
