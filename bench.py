@@ -665,6 +665,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g2 = make(probs, cost_dtype=cost_dtype, diag="never", **ext)
+        t_created = time.perf_counter()
         nsteps = args.warmup + args.steps
         g2.step(nsteps)
         pbar = g2.barycenter()
@@ -678,7 +679,9 @@ def main():
                        "h2d_bytes_per_step": h2d / nsteps,
                        "d2h_bytes_per_step": pbar.nbytes / nsteps,
                        "what": f"mam_create from host arrays + {nsteps} mam_step + "
-                               "mam_get_barycenter to host, wall clock"}
+                               "mam_get_barycenter to host, wall clock",
+                       "create_ms": (t_created - t0) * 1e3,
+                       "steps_and_read_ms": (t0 + dt - t_created) * 1e3}
     SHARD = None
     if rank == 0 and ws == 1:
         if not args.no_extra and args.workload != 2:
