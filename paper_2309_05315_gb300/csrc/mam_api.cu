@@ -938,44 +938,60 @@ static mam_status build_cost_tabulated(mam_problem* h, const double* xi,
 // Columns c0 .. c1 - 1 whose cost columns repeat an earlier one: equal point
 // (bit for bit), alpha_m and eta give the same column.  reps: the columns to
 // build (global indices, first of each class); dst_src: (column, its class's
-// first column) for the others.
+// first column) for the others.  A point is keyed by the indices of its
+// coordinates among their distinct values, so this applies where those are
+// few (pixel grids); elsewhere every column is built.
 static void repeated_cost_columns(const std::vector<double>& zk, int dim, long long c0,
                                   long long c1, const std::vector<int>& col_meas,
                                   const std::vector<double>& alpha_m,
                                   const std::vector<double>& eta_m, std::vector<long long>& reps,
                                   std::vector<long long>& dst_src) {
   const long long n = c1 - c0;
-  const int w = dim + 2;
-  auto word = [&](long long j, int i) {
-    double v = i < dim ? zk[size_t(j) * dim + i]
-                       : (i == dim ? alpha_m[col_meas[c0 + j]] : eta_m[col_meas[c0 + j]]);
-    uint64_t b;
-    std::memcpy(&b, &v, sizeof b);
-    return b;
-  };
-  size_t cap = 64;
-  while (cap < 2 * size_t(n)) cap <<= 1;
-  std::vector<long long> slot(cap, -1);
   reps.clear();
   dst_src.clear();
+  auto all = [&]() {
+    reps.resize(size_t(n));
+    for (long long j = 0; j < n; ++j) reps[j] = c0 + j;
+    dst_src.clear();
+  };
+  std::vector<double> vals;
+  std::vector<int> idx[3];
+  long long nz[3] = {1, 1, 1};
+  long long key_span = 1;
+  for (int k = 0; k < dim; ++k) {
+    if (!distinct_values(zk.data() + k, size_t(n), size_t(dim), 4096, vals, idx[k])) return all();
+    nz[k] = (long long)vals.size();
+    key_span *= nz[k];
+  }
+  // (alpha_m, eta) classes of the measures of these columns
+  std::vector<int> mcls(alpha_m.size(), -1);
+  std::vector<std::pair<uint64_t, uint64_t>> cls;
   for (long long j = 0; j < n; ++j) {
-    uint64_t hsh = 0x9E3779B97F4A7C15ull;
-    for (int i = 0; i < w; ++i) hsh = (hsh ^ word(j, i)) * 0xff51afd7ed558ccdull;
-    size_t s = size_t(hsh ^ (hsh >> 31)) & (cap - 1);
-    for (;; s = (s + 1) & (cap - 1)) {
-      const long long k = slot[s];
-      if (k < 0) {
-        slot[s] = j;
-        reps.push_back(c0 + j);
-        break;
-      }
-      bool same = true;
-      for (int i = 0; i < w && same; ++i) same = word(j, i) == word(k, i);
-      if (same) {
-        dst_src.push_back(c0 + j);
-        dst_src.push_back(c0 + k);
-        break;
-      }
+    const int m = col_meas[c0 + j];
+    if (mcls[m] >= 0) continue;
+    uint64_t a, b;
+    std::memcpy(&a, &alpha_m[m], sizeof a);
+    std::memcpy(&b, &eta_m[m], sizeof b);
+    int c = 0;
+    while (c < int(cls.size()) && !(cls[c].first == a && cls[c].second == b)) ++c;
+    if (c == int(cls.size())) {
+      if (cls.size() == 64) return all();
+      cls.push_back({a, b});
+    }
+    mcls[m] = c;
+  }
+  if (key_span * (long long)cls.size() > (1LL << 24)) return all();
+  std::vector<int> first(size_t(key_span * (long long)cls.size()), -1);
+  for (long long j = 0; j < n; ++j) {
+    long long key = mcls[col_meas[c0 + j]];
+    for (int k = 0; k < dim; ++k) key = key * nz[k] + idx[k][j];
+    int& f = first[size_t(key)];
+    if (f < 0) {
+      f = int(j);
+      reps.push_back(c0 + j);
+    } else {
+      dst_src.push_back(c0 + j);
+      dst_src.push_back(c0 + f);
     }
   }
 }
