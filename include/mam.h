@@ -335,7 +335,10 @@ mam_status mam_get_pruned_sizes(const mam_problem* h, int32_t* S_out);
  * Infrastructure for long runs and for the autotuner: the paper has no
  * counterpart (its state is the plan theta^k of Algorithm 1).  A sharded
  * handle saves and restores its own measures; every rank must restore the
- * same iteration. */
+ * same iteration.  With the sparse plan layout the blob holds each column's
+ * pairs and count and each measure's last shift in place of theta, and
+ * restores only into a handle of the same layout and sparse_slots
+ * (MAM_ERR_INVALID_ARG otherwise). */
 mam_status mam_get_state(mam_problem* h, void* buf, size_t* bytes);
 mam_status mam_set_state(mam_problem* h, const void* buf, size_t bytes);
 
