@@ -802,23 +802,27 @@ mam_status prime_thresholds(mam_problem* h) {
     a.amask = nullptr;
     MAM_CUDA(launch_column_step(h, a, false), "threshold priming");
   }
-  float* keep = nullptr;
-  MAM_CUDA(cudaMalloc(&keep, sizeof(float) * size_t(h->T)), "cudaMalloc (thresholds)");
-  mam_status s = MAM_OK;
-  cudaError_t e = cudaMemcpyAsync(keep, h->lam, sizeof(float) * size_t(h->T),
-                                  cudaMemcpyDeviceToDevice, h->stream);
-  if (e != cudaSuccess) s = cuda_fail(h, e, "threshold copy");
-  if (s == MAM_OK) s = reset_state(h);
-  if (s == MAM_OK) {
-    e = cudaMemcpyAsync(h->lam, keep, sizeof(float) * size_t(h->T), cudaMemcpyDeviceToDevice,
-                        h->stream);
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(h->passes, 0, sizeof(unsigned long long), h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) s = cuda_fail(h, e, "threshold copy");
+  // The passes changed the plans, the row-sum accumulators, the counters
+  // and t (not the marginals, p or the shifts, which only the averaging
+  // writes): restore those to the state of theta^0 and keep the thresholds.
+  if (h->sparse) {
+    MAM_CUDA(launch_init_sparse(h->sp_cnt, h->th0, nullptr, h->q64, h->T, h->R,
+                                h->theta0_mode, h->stream),
+             "init kernel");
+  } else {
+    MAM_CUDA(launch_init_theta(h->theta, nullptr, h->q64, h->T, h->R, h->ld, h->theta0_mode,
+                               h->stream),
+             "init kernel");
   }
-  cudaFree(keep);
-  return s;
+  MAM_CUDA(cudaMemsetAsync(h->acc, 0, sizeof(unsigned long long) * size_t(h->Mtot) * h->R,
+                           h->stream),
+           "memset");
+  MAM_CUDA(cudaMemsetAsync(h->iter_d, 0, sizeof(long long), h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->done, 0, sizeof(unsigned), h->stream), "memset");
+  MAM_CUDA(cudaMemsetAsync(h->passes, 0, sizeof(unsigned long long), h->stream), "memset");
+  std::vector<double> ones(h->P, 1.0);
+  MAM_TRY(upload(h, h->t_used, ones.data(), ones.size()));
+  return sync(h);
 }
 
 // Generated costs: FP32 copies of the points, the barycenter points as

@@ -129,7 +129,7 @@ __global__ void copy_cost_columns_kernel(uint4* cost, const long long* dst_src, 
 
 // theta^0 (Alg. 1 Step 0; "Initialization" leaves it arbitrary):
 // mode 0: theta_rs = q_s / R, mode 1: 0.  Padding rows are 0 and every
-// threshold starts unknown (NaN).
+// threshold starts unknown (NaN; lam = null keeps the thresholds).
 __global__ void init_theta_kernel(float* theta, float* lam,
                                   const double* q, long long T, int R, int ld,
                                   int mode) {
@@ -144,7 +144,7 @@ __global__ void init_theta_kernel(float* theta, float* lam,
       th[g] = make_float4(r < R ? v : 0.f, r + 1 < R ? v : 0.f, r + 2 < R ? v : 0.f,
                           r + 3 < R ? v : 0.f);
     }
-    if (threadIdx.x == 0) lam[col] = __int_as_float(0x7fc00000);
+    if (lam && threadIdx.x == 0) lam[col] = __int_as_float(0x7fc00000);
   }
 }
 

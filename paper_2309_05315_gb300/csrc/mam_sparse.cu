@@ -19,14 +19,15 @@ namespace mam {
 namespace {
 
 // theta^0 of Step 0 ("Initialization" leaves it arbitrary): mode 0 holds
-// q_s / R on every row (rounded once to FP32), mode 1 holds 0.
+// q_s / R on every row (rounded once to FP32), mode 1 holds 0.  The thresholds
+// become unknown (NaN) unless lam is null.
 __global__ void init_sparse_kernel(int* cnt, float* th0, float* lam, const double* q,
                                    long long T, int R, int mode) {
   for (long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x; col < T;
        col += (long long)gridDim.x * blockDim.x) {
     cnt[col] = -1;
     th0[col] = mode == 0 ? float(q[col] / double(R)) : 0.f;
-    lam[col] = __int_as_float(0x7fc00000);
+    if (lam) lam[col] = __int_as_float(0x7fc00000);
   }
 }
 

@@ -129,6 +129,8 @@ def unsharded(Mam, prob, iters, **kw):
     (2, dict()),
     (3, dict()),
     (2, dict(n_bundles=3, seed=9)),
+    (2, dict(plan_layout="sparse")),
+    (3, dict(plan_layout="sparse", n_bundles=3, seed=9)),
 ])
 def test_sharded_balanced_is_bitwise_unsharded(Mam, n, kw):
     prob = tiny_problem(500, M=6, K=8, rho=6.0)
