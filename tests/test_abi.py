@@ -156,3 +156,34 @@ def test_generated_and_shared_layouts_need_positive_alpha(L):
     h = C.c_void_p()
     assert L.mam_create(C.byref(d), C.byref(h)) == 1
     assert b"alpha_m > 0" in L.mam_last_error(None)
+
+
+@pytest.mark.parametrize("case", [
+    dict(plan_layout=2),
+    dict(plan_layout=1, sparse_slots=3),      # odd
+    dict(plan_layout=1, sparse_slots=-2),
+    dict(plan_layout=1, sparse_slots=10),     # above round_up(R, 8) = 8
+    dict(sparse_slots=8),                     # slots without the sparse layout
+    dict(plan_layout=1, cost_layout=2),       # generated costs
+])
+def test_invalid_plan_layout_fields(L, case):
+    d, keep = make_desc(**case)
+    h = C.c_void_p()
+    assert L.mam_create(C.byref(d), C.byref(h)) == 1
+    assert not h.value
+    assert len(L.mam_last_error(None)) > 0
+
+
+def test_sparse_layout_needs_one_cta_per_column(L):
+    """The sparse plan layout runs on the one-CTA-per-column kernel: R up to
+    12288 (round_up(R, 8) <= 12288)."""
+    d, keep = make_desc(R=12289, plan_layout=1)
+    h = C.c_void_p()
+    assert L.mam_create(C.byref(d), C.byref(h)) == 1
+    assert b"12288" in L.mam_last_error(None)
+    d, keep = make_desc(R=12288, plan_layout=1)
+    h = C.c_void_p()
+    st = L.mam_create(C.byref(d), C.byref(h))  # valid: fails later without a GPU
+    assert st != 1, L.mam_last_error(None)
+    if h.value:
+        L.mam_destroy(h)
