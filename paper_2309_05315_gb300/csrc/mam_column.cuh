@@ -14,6 +14,26 @@
 namespace mam {
 namespace {
 
+// Sparse plans, one float4 group of rows r0 .. r0 + 3 with an active row:
+// the Step 3 row sums of its active rows and their (row, pihat) pairs, a slot
+// each from the column's shared-memory counter (the order of the pairs is
+// immaterial; slots past K are counted, not written).  Not inlined: active
+// groups are few, and the column kernel's loop stays small enough for the
+// instruction cache.
+__device__ __noinline__ void sparse_commit_group(const float (&pv)[4], int r0,
+                                                 unsigned long long* acc, float fx,
+                                                 int* counter, int2* dst, int K) {
+  int slot = atomicAdd(counter, int(pv[0] > 0.f) + int(pv[1] > 0.f) + int(pv[2] > 0.f) +
+                                    int(pv[3] > 0.f));
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (pv[e] > 0.f) {
+      atomicAdd(acc + r0 + e, (unsigned long long)f32_to_i64_rn(pv[e] * fx));
+      if (slot < K) dst[slot] = make_int2(r0 + e, __float_as_int(pv[e]));
+      ++slot;
+    }
+}
+
 // ------------------------------------------------------- column kernel
 
 // Step 2 of Algorithm 1 for one CTA's slice of the index set, one column at
@@ -53,35 +73,16 @@ namespace {
 // SP: the sparse plan layout.  Every step sets theta' = pihat - d with pihat
 // zero off the active set, so a column is stored as the (row, value) pairs
 // of its pihat and each measure keeps the d of its last visit (d_last,
-// written by the averaging kernel).  One theta tile per CTA holds -d_last of
-// the current measure; a column's pairs arrive with its cost (one bulk copy
-// of round_up(count, 2) pairs), are scattered into the tile as
-// value + (-d_last_r) -- the FP32 value the dense layout stores -- before
+// written by the averaging kernel).  One theta tile per CTA holds 0 - d_last
+// of the current measure; a column's pairs arrive with its cost (one bulk
+// copy of round_up(count, 2) pairs), are scattered into the tile as
+// value + (0 - d_last_r) -- the FP32 value the dense layout stores -- before
 // pass 1 and restored after it, so pass 1 reads the column's theta from the
-// tile.  A column never visited holds theta^0 (count -1: q_s / R, or 0).
-// The commit writes the new pairs (slots taken per warp from a shared-memory
-// counter, order immaterial) instead of theta; the count is stored once the
-// next barrier has passed.  Stages must be 1.
-// Sparse plans, one float4 group of rows r0 .. r0 + 3 with an active row:
-// the Step 3 row sums of its active rows and their (row, pihat) pairs, a slot
-// each from the column's shared-memory counter (the order of the pairs is
-// immaterial; slots past K are counted, not written).  Not inlined: active
-// groups are few, and the column kernel's loop stays small enough for the
-// instruction cache.
-__device__ __noinline__ void sparse_commit_group(const float (&pv)[4], int r0,
-                                                 unsigned long long* acc, float fx,
-                                                 int* counter, int2* dst, int K) {
-  int slot = atomicAdd(counter, int(pv[0] > 0.f) + int(pv[1] > 0.f) + int(pv[2] > 0.f) +
-                                    int(pv[3] > 0.f));
-#pragma unroll
-  for (int e = 0; e < 4; ++e)
-    if (pv[e] > 0.f) {
-      atomicAdd(acc + r0 + e, (unsigned long long)f32_to_i64_rn(pv[e] * fx));
-      if (slot < K) dst[slot] = make_int2(r0 + e, __float_as_int(pv[e]));
-      ++slot;
-    }
-}
-
+// tile.  A column never visited (count -1) fills the tile with theta^0
+// (q_s / R, or 0) and refills it with 0 - d_last afterwards.  The commit
+// skips groups without an active row and writes a pair per active row
+// (sparse_commit_group) instead of theta; the count is stored once the next
+// barrier has passed.  Stages must be 1.
 template <int NV, typename CT, bool DIAG, bool SP>
 __global__ void __launch_bounds__(MaxThreads<NV>::value, MinCtas<NV>::value)
     column_kernel(const ColArgs A) {
