@@ -135,6 +135,15 @@ def test_general_cost_matrix(Mam):
     compare_trajectory(Mam, prob, 30)
 
 
+def test_repeated_points_with_unequal_alpha(Mam):
+    """Measures on one pixel grid with alpha = (0.25, 0.5, 0.25): creation
+    builds each (point, alpha_m) class of cost columns once and copies it to
+    the other columns of the class, so the first and third measures share
+    cost columns while the second keeps its own."""
+    prob = tiny_problem(41, M=3, K=10, rho=20.0, density=0.9, alpha=[0.25, 0.5, 0.25])
+    compare_trajectory(Mam, prob, 25)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_tabulated_cost_equals_direct_formula(Mam, dtype):
     """Pixel-grid points take few values per coordinate, so creation builds
